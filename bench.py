@@ -1,0 +1,309 @@
+"""Benchmark: cells x CFD-step / s of the batched stiff-chemistry integrator.
+
+One step = one chem_integrate call over the whole batch (every cell advanced by
+one CFD time step dt at rtol 1e-8, atol 1e-12), from the same saved input state
+each time. Default workload: the 54-species / 270-reaction synthetic mechanism,
+65,536 cells at 60 bar (60 % cold, 30 % igniting, 10 % burnt), dt = 1e-6 s.
+
+Forms timed on the GPU:
+  plain_fp64 : FP64 throughout, one CTA per cell (the plain batched baseline)
+  headline   : mixed precision (FP32 LU/solves + FP64 refinement), persistent
+               work queue, and (when trained) the learned cost order and initial
+               step.
+The JSON line's value is the headline form; plain_fp64 is reported beside it.
+
+--impl reference times the CPU oracle (the plain FP64 C++ restatement of the
+method) on a bounded sample of the same workload on this machine's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2112_05834_gb300 import synth  # noqa: E402
+
+RTOL, ATOL = 1e-8, 1e-12
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (no FP64 figure in the measured peaks)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c54_65k")
+    ap.add_argument("--cells", type=int, default=None, help="override the number of cells")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU baseline time budget")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--forms", default="plain_fp64,headline")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------- helpers
+def algorithmic_fp64_flops_per_step(m, precision, ir_sweeps):
+    """Algorithmic FP64 floating-point operations of one Rosenbrock step of one cell.
+
+    Counted from the method's structure (exp/log not counted as flops):
+      RHS (6 per step + 1 at the Jacobian point): per species 41 (thermo
+        polynomials, concentration, production sum share, enthalpy sums), per
+        reaction 22 (rate argument, mass-action products, reverse ratio, net
+        rate, production scatter), per third-body reaction 2 K ([M] sums), per
+        falloff reaction 30 (Pr, broadening);
+      Jacobian data at the step point: 24 per reaction; assembly 6 n^2;
+      FP64 form: LU 2 n^3 / 3, 6 solves x 2 n^2, iteration matrix n^2;
+      mixed form: 6 solves x ir_sweeps x 2 n^2 refinement residuals (LU and
+        triangular solves run in FP32 and are not counted here).
+    """
+    K, I = m.n_species, m.n_reactions
+    n = K + 1
+    n_tb = int(np.sum(m.rxn_type >= 1))
+    n_fo = int(np.sum(m.rxn_type >= 2))
+    rhs = 41 * K + 22 * I + 2 * n_tb * K + 30 * n_fo
+    w = 7 * rhs + 24 * I + 6 * n * n
+    if precision == 0:
+        w += 2 * n ** 3 / 3 + 12 * n * n + n * n
+    else:
+        w += 6 * ir_sweeps * 2 * n * n
+    return float(w)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip() == "Active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_baseline(m, st, dt, seconds, seed=0):
+    """Oracle on a bounded uniform sample of the workload's cells (all host cores)."""
+    import oracle
+
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(st.T.shape[0])
+    done, t0 = 0, time.perf_counter()
+    chunk = 64
+    threads = oracle.max_threads()
+    while time.perf_counter() - t0 < seconds and done < order.size:
+        idx = order[done:done + chunk]
+        oracle.integrate(m, st.T[idx], st.p[idx], st.Y[idx], dt, RTOL, ATOL, n_threads=threads)
+        done += idx.size
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": "cells*step/s", "cores": threads, "kind": "oracle",
+            "sample": f"{done} uniformly sampled cells of the {st.T.shape[0]}-cell batch, "
+                      f"{el:.1f} s on {threads} threads"}
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_2112_05834_gb300 as pkg
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    m, st, dt = synth.workload(args.workload, n_cells=args.cells)
+    n = st.T.shape[0]
+    T0 = torch.tensor(st.T, device=dev)
+    p = torch.tensor(st.p, device=dev)
+    Y0 = torch.tensor(st.Y, device=dev)
+    T = torch.empty_like(T0)
+    Y = torch.empty_like(Y0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    forms = {}
+    plain = pkg.Integrator(m, precision=0, scheduler=0)
+    head = pkg.Integrator(m, precision=1, scheduler=2, ir_sweeps=2)
+    learned = False
+    if not args.no_learned and hasattr(pkg, "train_cost_model"):
+        learned = pkg.train_cost_model(head, m, args.workload, n, dt, seed=7)
+    want = args.forms.split(",")
+    if "plain_fp64" in want:
+        forms["plain_fp64"] = plain
+    if "headline" in want:
+        forms["headline"] = head
+
+    def one(integ):
+        T.copy_(T0)
+        Y.copy_(Y0)
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        integ.integrate(T, p, Y, dt, RTOL, ATOL)
+        e1.record(stream)
+        return e0, e1
+
+    results = {}
+    clocks = ClockSampler(dev.index)
+    clk = None
+    for name, integ in forms.items():
+        for _ in range(args.warmup):
+            one(integ)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        if name == "headline":
+            clocks.start()
+        evs = [one(integ) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        if name == "headline":
+            clk = clocks.stop()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        tot = integ.totals()
+        results[name] = {"ms_total": ms, "substeps": tot["substeps"], "failed": tot["failed"],
+                         "rejects": tot["rejects"]}
+    # end to end through the host entry point (H2D of T, p, Y; D2H of T, Y inside the call)
+    Th = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+    ph = torch.tensor(st.p).pin_memory().numpy()
+    Yh = torch.empty((n, m.n_species), dtype=torch.float64).pin_memory().numpy()
+    e2e_times = []
+    for it in range(args.warmup + args.steps):
+        Th[:] = st.T
+        Yh[:] = st.Y
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        head.integrate_host(Th, ph, Yh, dt, RTOL, ATOL)
+        t1 = time.perf_counter()
+        if it >= args.warmup:
+            e2e_times.append(t1 - t0)
+    e2e_s = sum(e2e_times)
+    if world > 1:
+        t = torch.tensor([results["headline"]["ms_total"], e2e_s], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        results["headline"]["ms_total"], e2e_s = float(t[0]), float(t[1])
+    return m, st, dt, n, results, clk, e2e_s, learned, head
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if world > 1:
+        import torch
+
+        torch.distributed.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        if rank == 0:
+            m, st, dt = synth.workload(args.workload, n_cells=args.cells)
+            vals = []
+            budget = max(2.0, args.cpu_seconds / max(1, args.steps))
+            for _ in range(args.steps):
+                vals.append(cpu_baseline(m, st, dt, budget, seed=len(vals))["value"])
+            cb = cpu_baseline(m, st, dt, budget, seed=99)
+            v = float(np.mean(vals))
+            line = {"impl": "reference", "metric": "cells*CFD-step/s at rtol 1e-8 (CPU oracle, FP64)",
+                    "value": v, "unit": "cells*step/s", "n_gpus": args.gpus, "steps": args.steps,
+                    "warmup": args.warmup, "ms_per_step": 1e3 * st.T.shape[0] / v, "higher_is_better": True,
+                    "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                    "config": {"workload": args.workload, "n_cells": int(st.T.shape[0]),
+                               "mechanism": f"{m.n_species} species / {m.n_reactions} reactions"},
+                    "cpu_baseline": {"value": v, "unit": "cells*step/s", "cores": cb["cores"], "kind": "oracle",
+                                     "sample": cb["sample"]},
+                    "e2e": {"value": v, "unit": "cells*step/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            print(json.dumps(line))
+        return
+    m, st, dt, n, res, clk, e2e_s, learned, head = run_ours(args, rank, world)
+    if rank != 0:
+        return
+    hd = res["headline"]
+    value = world * n * args.steps / (hd["ms_total"] / 1e3)
+    ms_per_step = hd["ms_total"] / args.steps
+    # roofline of the integration kernel (FP64 pipe): algorithmic FP64 flops / time
+    w_step = algorithmic_fp64_flops_per_step(m, 1, 2)
+    substeps_per_launch = hd["substeps"]  # totals of the last launch
+    achieved = w_step * substeps_per_launch / (ms_per_step / 1e3) / 1e12
+    line = {
+        "metric": "cells*CFD-step/s at rtol 1e-8 (mixed+learned vs plain FP64 GPU)",
+        "value": value, "unit": "cells*step/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": args.workload, "n_cells": n,
+                   "mechanism": f"{m.n_species} species / {m.n_reactions} reactions (seeded synthetic)",
+                   "pressure_bar": float(st.p[0] / 1e6), "dt_s": dt, "rtol": RTOL, "atol": ATOL,
+                   "form": "mixed precision + queue" + (" + learned order/h0" if learned else ""),
+                   "l2": "flushed (256 MB write) before every step", "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "plain_fp64": None,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "note": "FP64 pipe; algorithmic FP64 flops per launch / launch time; peak = nominal GB300 FP64"},
+        "clocks": clk,
+        "e2e": {"value": world * n * args.steps / e2e_s, "unit": "cells*step/s",
+                "h2d_bytes_per_step": int(n * (m.n_species + 2) * 8), "d2h_bytes_per_step": int(n * (m.n_species + 1) * 8)},
+        "gpu_launches": None,
+        "substeps_per_step": hd["substeps"], "failed_cells": hd["failed"],
+    }
+    if "plain_fp64" in res:
+        pl = res["plain_fp64"]
+        pv = n * args.steps / (pl["ms_total"] / 1e3)
+        w0 = algorithmic_fp64_flops_per_step(m, 0, 0)
+        a0 = w0 * pl["substeps"] / (pl["ms_total"] / args.steps / 1e3) / 1e12
+        line["plain_fp64"] = {"value": pv, "ms_per_step": pl["ms_total"] / args.steps,
+                              "substeps_per_step": pl["substeps"],
+                              "roofline_fp64_frac": a0 / FP64_PEAK_TFLOPS, "achieved_tflops": a0}
+        line["speedup_vs_plain_fp64"] = value / pv
+    # integration kernel per step, plus (learned form) features, 2 GEMMs, head, 3 sort kernels
+    line["gpu_launches"] = args.steps * (1 + (7 if learned else 0))
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(m, st, dt, args.cpu_seconds)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,242 @@
+/*
+ * chem.h - C ABI of the GB300 batched stiff-chemistry integrator.
+ *
+ * The library advances, for every cell of a batch, the constant-pressure
+ * adiabatic finite-rate kinetics ODE  f = d(phi)/dt  (paper: Introduction,
+ * composition vector phi and f = d phi / dt) over one CFD time step dt. Each
+ * cell is integrated by an adaptive Rosenbrock method (RODAS4) whose iteration
+ * matrix (I/(h gamma) - J) uses the fully analytical Jacobian
+ * J_ij = d f_i / d phi_j (paper: Methodology, "Analytical Jacobian and improved
+ * ODE solution") and is handled by dense LU decomposition with partial
+ * pivoting and forward/back substitution (same section: LU decomposition and
+ * back substitution). The uneven per-cell cost that the paper balances across
+ * MPI ranks (Methodology, "DLBFoam: Dynamic load balancing") is balanced inside
+ * one GPU by a device work queue, optionally ordered by a learned cost model.
+ *
+ * State vector per cell: y = [T, Y_1 .. Y_K] (K+1 unknowns); p is constant
+ * over the step. Units: cgs-molar (mol, cm^3, s, K, erg, dyn/cm^2).
+ *
+ * Conventions for every entry point:
+ *   - Return value: chem_status. CHEM_OK on success; argument errors are
+ *     detected before any GPU work and return CHEM_ERR_INVALID_ARG; the message
+ *     is available from chem_last_error(handle).
+ *   - "device" pointers are CUDA device (or managed) memory of the current
+ *     device; "host" pointers are CPU memory (pinned memory makes copies
+ *     asynchronous). The library never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream. Integration calls are stream-ordered and return after enqueueing
+ *     unless stated otherwise.
+ *   - No entry point aborts the process or traps on the GPU. Per-cell failures
+ *     are recorded as per-cell status codes (see chem_cell_status).
+ *   - A handle may be used from one host thread / one stream at a time.
+ */
+#ifndef CHEM_H_
+#define CHEM_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct chem_handle_s* chem_handle;
+
+typedef enum {
+  CHEM_OK = 0,
+  CHEM_ERR_INVALID_ARG = 1,
+  CHEM_ERR_BAD_MECHANISM = 2,
+  CHEM_ERR_CUDA = 3,
+  CHEM_ERR_CELLS_FAILED = 4,
+  CHEM_ERR_OOM = 5
+} chem_status;
+
+/* Per-cell outcome of an integration (chem_get_stats, cell_status array). */
+typedef enum {
+  CHEM_CELL_OK = 0,          /* reached dt; T recovered from the conserved enthalpy */
+  CHEM_CELL_MAX_STEPS = 1,   /* step budget (option "max_steps") exhausted */
+  CHEM_CELL_H_UNDERFLOW = 2, /* step size fell below 1e-20 s */
+  CHEM_CELL_NONFINITE = 3,   /* non-finite input state */
+  CHEM_CELL_T_RANGE = 4      /* final T outside [200, 6000] K */
+} chem_cell_status;
+
+/*
+ * Reaction mechanism tables (host pointers, copied at chem_create; the caller
+ * keeps ownership). K species, I reactions, E elements.
+ *   W[K]                 molecular weights, g/mol (must equal sum of atomic masses
+ *                        in the caller's convention; checked for positivity)
+ *   elem[K][E]           atom counts (int32), used to check that every reaction
+ *                        balances every element
+ *   nasa_lo/hi[K][7]     NASA-7 coefficients a1..a7 below / above T_mid
+ *   T_lo/T_mid/T_hi[K]   validity range and switch temperature, K
+ *   rxn_type[I]          0 elementary, 1 third-body (+M), 2 Lindemann, 3 Troe falloff
+ *   reac_idx/reac_nu[I][2], prod_idx/prod_nu[I][2]
+ *                        up to two distinct species per side with coefficient 1 or
+ *                        2 (index -1 = empty slot); total order per side <= 2
+ *   reversible[I]        nonzero: reverse rate from the equilibrium constant
+ *   A, b, Ea_R [I]       k = A T^b exp(-Ea_R/T) (high-pressure limit for falloff)
+ *   A0, b0, Ea0_R [I]    low-pressure limit (falloff only)
+ *   troe[I][4]           alpha, T***, T*, T** (T** <= 0: that term absent)
+ *   eff[I][K]            third-body efficiencies (read for types 1..3)
+ */
+typedef struct {
+  int32_t n_species, n_reactions, n_elements;
+  const double* W;
+  const int32_t* elem;
+  const double *nasa_lo, *nasa_hi;
+  const double *T_lo, *T_mid, *T_hi;
+  const int32_t* rxn_type;
+  const int32_t *reac_idx, *reac_nu, *prod_idx, *prod_nu;
+  const int32_t* reversible;
+  const double *A, *b, *Ea_R;
+  const double *A0, *b0, *Ea0_R;
+  const double* troe;
+  const double* eff;
+} chem_mechanism_desc;
+
+/*
+ * Validates the mechanism (index ranges, coefficients, element balance of every
+ * reaction, positive W and Arrhenius prefactors, H/RT and S/R continuity at T_mid
+ * within 1e-6), builds the device tables on the current device and returns a
+ * handle in *out. Errors: CHEM_ERR_INVALID_ARG (NULL pointers),
+ * CHEM_ERR_BAD_MECHANISM (validation; message via chem_last_error(NULL)),
+ * CHEM_ERR_CUDA / CHEM_ERR_OOM.
+ */
+chem_status chem_create(const chem_mechanism_desc* desc, chem_handle* out);
+
+/* Frees the handle and its device memory (synchronises the device first). */
+chem_status chem_destroy(chem_handle h);
+
+/*
+ * Integrates n_cells cells over [0, dt] at relative/absolute tolerances
+ * rtol/atol (weighted RMS norm of the embedded error, scale atol + rtol*|y|).
+ *   T[n_cells]          device, in/out: temperature, K
+ *   p[n_cells]          device, in: pressure, dyn/cm^2
+ *   Y[n_cells][K]       device, in/out: mass fractions, cell-major contiguous
+ * A failed cell keeps its last accepted state and records its status; query
+ * with chem_get_stats. n_cells == 0 is a no-op. Errors: CHEM_ERR_INVALID_ARG
+ * (n_cells < 0, NULL pointers with n_cells > 0, dt <= 0, rtol <= 0, atol < 0,
+ * non-finite arguments), CHEM_ERR_CUDA.
+ */
+chem_status chem_integrate(chem_handle h, int64_t n_cells, double* T, const double* p, double* Y,
+                           double dt, double rtol, double atol, void* stream);
+
+/*
+ * As chem_integrate, but T, p, Y are HOST arrays: the call copies them to
+ * handle-owned device buffers, integrates, copies T and Y back and synchronises
+ * `stream` before returning.
+ */
+chem_status chem_integrate_host(chem_handle h, int64_t n_cells, double* T, const double* p,
+                                double* Y, double dt, double rtol, double atol, void* stream);
+
+/* One batch of cells of one mechanism; pointers as in chem_integrate. */
+typedef struct {
+  chem_handle h;
+  int64_t n_cells;
+  double* T;
+  const double* p;
+  double* Y;
+} chem_job;
+
+/*
+ * Integrates up to 8 jobs (each with its own mechanism handle) in ONE kernel
+ * launch sharing one work queue. Options (precision, scheduler, block size)
+ * are taken from jobs[0].h; per-cell statistics go to each job's handle.
+ */
+chem_status chem_integrate_jobs(const chem_job* jobs, int32_t n_jobs, double dt, double rtol,
+                                double atol, void* stream);
+
+/*
+ * Handle options (numeric values):
+ *   "precision"   0 = FP64 throughout;
+ *                 1 = mixed: LU and triangular solves in FP32, every solve
+ *                 refined by FP64 iterative refinement against the FP64-assembled
+ *                 iteration matrix (state, rates, exp/log, error control in FP64);
+ *                 2 = as 1 but with the Jacobian assembled in FP32 and the
+ *                 refinement residual taken against that FP32 matrix
+ *   "ir_sweeps"   0..3 refinement sweeps per solve in precision 1 and 2 (default 2)
+ *   "scheduler"   0 = plain (one CTA per cell, hardware block order),
+ *                 1 = static (persistent CTAs, fixed round-robin cells),
+ *                 2 = queue (persistent CTAs pulling cells from a device counter)
+ *   "order"       0 = cell index order; 1 = learned cost order (needs a trained
+ *                 model, see chem_mlp_*); 2 = last-call cost order
+ *   "h0"          0 = starting-step heuristic; 1 = learned initial step
+ *   "max_steps"   step budget per cell (default 100000)
+ *   "block"       threads per cell: 64, 128 or 256 (default 128)
+ *   "ctas_per_sm" resident CTAs per SM for persistent schedulers (0 = maximum)
+ *   "graph"       1 = capture the launch sequence in a CUDA graph and replay it
+ *                 while arguments repeat
+ *   "autotune"    1 = time block sizes on a sample at the first call for a
+ *                 new size and keep the fastest
+ * Errors: CHEM_ERR_INVALID_ARG for an unknown key or out-of-range value.
+ */
+chem_status chem_set_option(chem_handle h, const char* key, double value);
+chem_status chem_get_option(chem_handle h, const char* key, double* value);
+
+/*
+ * Copies per-cell statistics of the handle's last integration into the given
+ * DEVICE arrays (each may be NULL; length >= that call's n_cells), synchronises
+ * `stream`, and returns CHEM_ERR_CELLS_FAILED if any cell's status is not
+ * CHEM_CELL_OK. substeps counts accepted and rejected steps; h_first is the
+ * first accepted step size (s).
+ */
+chem_status chem_get_stats(chem_handle h, void* stream, int32_t* substeps, int32_t* rejects,
+                           double* h_first, int32_t* cell_status);
+
+/* Totals of the last integration (host outputs, any may be NULL); synchronises. */
+chem_status chem_get_totals(chem_handle h, void* stream, int64_t* n_cells, int64_t* substeps,
+                            int64_t* rejects, int64_t* failed);
+
+/* Last error message of the handle (or of the last chem_create when h is NULL). */
+const char* chem_last_error(chem_handle h);
+
+/* Number of species / reactions of a handle. */
+int32_t chem_n_species(chem_handle h);
+int32_t chem_n_reactions(chem_handle h);
+
+/* ------------------------------------------------------------------------
+ * Diagnostic entry points: the same device code the integrator runs, exposed
+ * for parity testing against an independent CPU implementation.
+ * ------------------------------------------------------------------------ */
+
+/* f[n_cells][K+1] = RHS at the given states (device pointers). */
+chem_status chem_eval_rhs(chem_handle h, int64_t n_cells, const double* T, const double* p,
+                          const double* Y, double* f, void* stream);
+
+/*
+ * J[n_cells][K+1][K+1] (row-major) = analytical Jacobian at the given states.
+ * With option precision = 2 the Jacobian is assembled in FP32 and returned
+ * widened to double.
+ */
+chem_status chem_eval_jacobian(chem_handle h, int64_t n_cells, const double* T, const double* p,
+                               const double* Y, double* J, void* stream);
+
+/* h0[n_cells] = starting step of the heuristic used by chem_integrate. */
+chem_status chem_eval_h0(chem_handle h, int64_t n_cells, const double* T, const double* p,
+                         const double* Y, double dt, double rtol, double atol, double* h0,
+                         void* stream);
+
+/*
+ * Batched dense solve with the integrator's LU and triangular-solve code:
+ * for each of n_mat systems, A[dim][dim] x = b (device, row-major, A unchanged).
+ * precision 0: FP64 LU; 1: FP32 LU of A with `ir_sweeps` FP64 refinement sweeps
+ * against A; 2: as 1 against A rounded to FP32.
+ * info[n_mat] (device, may be NULL): 0, or 1+k for a zero pivot at column k.
+ * dim <= 128.
+ */
+chem_status chem_lu_solve_batched(int64_t n_mat, int32_t dim, const double* A, const double* b,
+                                  double* x, int32_t* info, int32_t precision, int32_t ir_sweeps,
+                                  void* stream);
+
+/*
+ * The Rosenbrock coefficients the device code uses, in the transformed form
+ * (Hairer & Wanner II, Sec. IV.7): gamma, a[6][6], c[6][6] (row-major,
+ * strictly lower), m[6] (solution weights), e[6] (error weights). Host only;
+ * needs no GPU.
+ */
+void chem_rosenbrock_tableau(double* gamma, double* a, double* c, double* m, double* e);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHEM_H_ */

@@ -653,7 +653,7 @@ CellResult integrate_cell(const OMech& m, double p, double* y, double dt, double
   while (true) {
     if (dt - t <= 1e-12 * dt) break;
     if (r.substeps >= max_steps) { r.status = ST_MAX_STEPS; break; }
-    if (h < h_min) { r.status = ST_H_UNDERFLOW; break; }
+    if (!(h >= h_min)) { r.status = ST_H_UNDERFLOW; break; }
     if (t + h > dt) h = dt - t;
     int bad = rodas_step(m, p, y, h, y1.data(), yh.data());
     r.substeps++;

@@ -1,0 +1,723 @@
+// Host side of the C ABI declared in include/chem.h: mechanism validation and
+// device-table construction, handle options, launch configuration, per-cell
+// statistics and the diagnostic entry points.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "chem.h"
+#include "chem_capi_internal.h"
+#include "chem_internal.h"
+#include "chem_kernels.h"
+#include "chem_mlp_internal.h"
+#include "rodas4.h"
+
+using namespace chem;
+
+static thread_local std::string g_create_error;
+
+static std::string cuda_msg(const char* what, cudaError_t e) {
+  return std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+}
+
+#define CHEM_CUDA(h, call)                                   \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) {                                 \
+      (h)->err = cuda_msg(#call, e_);                        \
+      return e_ == cudaErrorMemoryAllocation ? CHEM_ERR_OOM : CHEM_ERR_CUDA; \
+    }                                                        \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// mechanism validation
+// ---------------------------------------------------------------------------
+static double h_RT(const double* a, double T) {
+  return a[0] + a[1] * T / 2 + a[2] * T * T / 3 + a[3] * T * T * T / 4 + a[4] * T * T * T * T / 5 + a[5] / T;
+}
+static double s_R(const double* a, double T) {
+  return a[0] * std::log(T) + a[1] * T + a[2] * T * T / 2 + a[3] * T * T * T / 3 + a[4] * T * T * T * T / 4 + a[6];
+}
+
+static std::string validate(const chem_mechanism_desc* d) {
+  const int K = d->n_species, I = d->n_reactions, E = d->n_elements;
+  char buf[256];
+  if (K < 1 || K > 255) return "n_species must be in [1, 255]";
+  if (I < 0) return "n_reactions must be >= 0";
+  if (E < 0) return "n_elements must be >= 0";
+  if (!d->W || !d->nasa_lo || !d->nasa_hi || !d->T_lo || !d->T_mid || !d->T_hi)
+    return "NULL species table";
+  if (E > 0 && !d->elem) return "NULL element table";
+  if (I > 0 && (!d->rxn_type || !d->reac_idx || !d->reac_nu || !d->prod_idx || !d->prod_nu ||
+                !d->reversible || !d->A || !d->b || !d->Ea_R || !d->A0 || !d->b0 || !d->Ea0_R ||
+                !d->troe || !d->eff))
+    return "NULL reaction table";
+  for (int k = 0; k < K; ++k) {
+    if (!(d->W[k] > 0.0) || !std::isfinite(d->W[k])) {
+      snprintf(buf, sizeof buf, "species %d: molecular weight must be positive", k);
+      return buf;
+    }
+    if (!(d->T_lo[k] < d->T_mid[k] && d->T_mid[k] < d->T_hi[k])) {
+      snprintf(buf, sizeof buf, "species %d: need T_lo < T_mid < T_hi", k);
+      return buf;
+    }
+    for (int a = 0; a < 7; ++a)
+      if (!std::isfinite(d->nasa_lo[7 * k + a]) || !std::isfinite(d->nasa_hi[7 * k + a])) {
+        snprintf(buf, sizeof buf, "species %d: non-finite NASA coefficient", k);
+        return buf;
+      }
+    const double Tm = d->T_mid[k];
+    const double hl = h_RT(d->nasa_lo + 7 * k, Tm), hh = h_RT(d->nasa_hi + 7 * k, Tm);
+    const double sl = s_R(d->nasa_lo + 7 * k, Tm), sh = s_R(d->nasa_hi + 7 * k, Tm);
+    if (std::fabs(hl - hh) > 1e-6 * std::max(1.0, std::fabs(hl)) ||
+        std::fabs(sl - sh) > 1e-6 * std::max(1.0, std::fabs(sl))) {
+      snprintf(buf, sizeof buf, "species %d: H/RT or S/R discontinuous at T_mid", k);
+      return buf;
+    }
+  }
+  for (int i = 0; i < I; ++i) {
+    const int t = d->rxn_type[i];
+    if (t < 0 || t > 3) {
+      snprintf(buf, sizeof buf, "reaction %d: unknown type %d", i, t);
+      return buf;
+    }
+    for (int side = 0; side < 2; ++side) {
+      const int32_t* idx = side ? d->prod_idx : d->reac_idx;
+      const int32_t* nu = side ? d->prod_nu : d->reac_nu;
+      int order = 0, nsp = 0;
+      for (int s = 0; s < 2; ++s) {
+        const int k = idx[2 * i + s];
+        if (k < 0) continue;
+        if (k >= K) {
+          snprintf(buf, sizeof buf, "reaction %d: species index %d out of range", i, k);
+          return buf;
+        }
+        if (nu[2 * i + s] < 1 || nu[2 * i + s] > 2) {
+          snprintf(buf, sizeof buf, "reaction %d: stoichiometric coefficient must be 1 or 2", i);
+          return buf;
+        }
+        order += nu[2 * i + s];
+        ++nsp;
+      }
+      if (nsp == 0 || order > 2) {
+        snprintf(buf, sizeof buf, "reaction %d: each side needs 1..2 species of total order <= 2", i);
+        return buf;
+      }
+      if (nsp == 2 && idx[2 * i] == idx[2 * i + 1]) {
+        snprintf(buf, sizeof buf, "reaction %d: repeated species must use coefficient 2", i);
+        return buf;
+      }
+    }
+    for (int e = 0; e < E; ++e) {
+      long bal = 0;
+      for (int s = 0; s < 2; ++s) {
+        if (d->reac_idx[2 * i + s] >= 0) bal -= (long)d->reac_nu[2 * i + s] * d->elem[d->reac_idx[2 * i + s] * E + e];
+        if (d->prod_idx[2 * i + s] >= 0) bal += (long)d->prod_nu[2 * i + s] * d->elem[d->prod_idx[2 * i + s] * E + e];
+      }
+      if (bal != 0) {
+        snprintf(buf, sizeof buf, "reaction %d: element %d not balanced", i, e);
+        return buf;
+      }
+    }
+    if (!(d->A[i] > 0.0) || !std::isfinite(d->b[i]) || !std::isfinite(d->Ea_R[i])) {
+      snprintf(buf, sizeof buf, "reaction %d: need A > 0 and finite b, Ea_R", i);
+      return buf;
+    }
+    if (t >= 2 && (!(d->A0[i] > 0.0) || !std::isfinite(d->b0[i]) || !std::isfinite(d->Ea0_R[i]))) {
+      snprintf(buf, sizeof buf, "reaction %d: falloff needs A0 > 0 and finite b0, Ea0_R", i);
+      return buf;
+    }
+    if (t == 3 && (!(d->troe[4 * i + 1] > 0.0) || !(d->troe[4 * i + 2] > 0.0) || !std::isfinite(d->troe[4 * i]))) {
+      snprintf(buf, sizeof buf, "reaction %d: Troe needs T*** > 0 and T* > 0", i);
+      return buf;
+    }
+    if (t >= 1)
+      for (int k = 0; k < K; ++k)
+        if (!std::isfinite(d->eff[(size_t)i * K + k]) || d->eff[(size_t)i * K + k] < 0.0) {
+          snprintf(buf, sizeof buf, "reaction %d: efficiencies must be finite and >= 0", i);
+          return buf;
+        }
+  }
+  return "";
+}
+
+// ---------------------------------------------------------------------------
+// device tables
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Pool {
+  std::vector<unsigned char> host;
+  size_t add(const void* src, size_t bytes) {
+    size_t off = (host.size() + 255) & ~(size_t)255;
+    host.resize(off + std::max<size_t>(bytes, 1));
+    if (bytes) std::memcpy(host.data() + off, src, bytes);
+    return off;
+  }
+};
+
+}  // namespace
+
+static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
+  const int K = d->n_species, I = d->n_reactions;
+  // sort reactions by kind so each warp meets at most a few kinds
+  std::vector<int> order(I);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return d->rxn_type[a] < d->rxn_type[b]; });
+  h->rxn_order = order;
+  std::vector<double> W(K), invW(K), nasa((size_t)36 * K, 0.0);
+  for (int k = 0; k < K; ++k) {
+    W[k] = d->W[k];
+    invW[k] = 1.0 / d->W[k];
+    for (int r = 0; r < 2; ++r) {
+      const double* a = (r == 0 ? d->nasa_lo : d->nasa_hi) + 7 * k;
+      double* o = &nasa[36 * k + 17 * r];
+      for (int j = 0; j < 5; ++j) o[j] = a[j];
+      o[5] = a[0];
+      o[6] = a[1] / 2.0;
+      o[7] = a[2] / 3.0;
+      o[8] = a[3] / 4.0;
+      o[9] = a[4] / 5.0;
+      o[10] = a[5];
+      o[11] = a[0];
+      o[12] = a[1];
+      o[13] = a[2] / 2.0;
+      o[14] = a[3] / 3.0;
+      o[15] = a[4] / 4.0;
+      o[16] = a[6];
+    }
+    nasa[36 * k + 34] = d->T_mid[k];
+  }
+  std::vector<double> arr((size_t)4 * I), fo, eff;
+  std::vector<int4> slots(I);
+  std::vector<int> rev(I);
+  std::vector<std::vector<int2>> sp(K), tr(K);
+  std::vector<std::vector<int4>> jr(K);
+  int n_tb = 0, n_fo = 0, i_tb0 = I, i_fo0 = I, i_troe0 = I;
+  for (int i = 0; i < I; ++i) {
+    const int o = order[i];
+    const int t = d->rxn_type[o];
+    if (t >= 1 && i_tb0 == I) i_tb0 = i;
+    if (t >= 2 && i_fo0 == I) i_fo0 = i;
+    if (t == 3 && i_troe0 == I) i_troe0 = i;
+    int sl[4] = {-1, -1, -1, -1};
+    int dnu = 0;
+    for (int side = 0; side < 2; ++side) {
+      const int32_t* idx = side ? d->prod_idx : d->reac_idx;
+      const int32_t* nu = side ? d->prod_nu : d->reac_nu;
+      int w = 2 * side;
+      for (int s = 0; s < 2; ++s) {
+        const int k = idx[2 * o + s];
+        if (k < 0) continue;
+        for (int c = 0; c < nu[2 * o + s]; ++c) sl[w++] = k;
+        dnu += side ? nu[2 * o + s] : -nu[2 * o + s];
+      }
+    }
+    slots[i] = make_int4(sl[0], sl[1], sl[2], sl[3]);
+    arr[4 * i + 0] = std::log(d->A[o]);
+    arr[4 * i + 1] = d->b[o];
+    arr[4 * i + 2] = d->Ea_R[o];
+    arr[4 * i + 3] = (double)dnu;
+    rev[i] = d->reversible[o] ? 1 : 0;
+    if (t >= 1) {
+      ++n_tb;
+      for (int k = 0; k < K; ++k) eff.push_back(d->eff[(size_t)o * K + k]);
+    }
+    if (t >= 2) {
+      ++n_fo;
+      const double* tr4 = d->troe + 4 * o;
+      const double f8[8] = {std::log(d->A0[o]), d->b0[o], d->Ea0_R[o], tr4[0], tr4[1], tr4[2],
+                            tr4[3], 0.0};
+      fo.insert(fo.end(), f8, f8 + 8);
+    }
+    // net stoichiometry per species
+    std::vector<std::pair<int, int>> nets;
+    for (int side = 0; side < 2; ++side) {
+      const int32_t* idx = side ? d->prod_idx : d->reac_idx;
+      const int32_t* nu = side ? d->prod_nu : d->reac_nu;
+      for (int s = 0; s < 2; ++s) {
+        const int k = idx[2 * o + s];
+        if (k < 0) continue;
+        const int v = side ? nu[2 * o + s] : -nu[2 * o + s];
+        bool found = false;
+        for (auto& pr : nets)
+          if (pr.first == k) { pr.second += v; found = true; }
+        if (!found) nets.push_back({k, v});
+      }
+    }
+    for (auto& pr : nets) {
+      if (pr.second == 0) continue;
+      sp[pr.first].push_back(make_int2(i, pr.second));
+      if (t >= 1) tr[pr.first].push_back(make_int2(i, pr.second));
+      for (int s = 0; s < 4; ++s)
+        if (sl[s] >= 0) jr[pr.first].push_back(make_int4(sl[s], i, pr.second, s));
+    }
+  }
+  auto flatten2 = [&](std::vector<std::vector<int2>>& v, std::vector<int>& ptr, std::vector<int2>& ent) {
+    ptr.assign(K + 1, 0);
+    for (int k = 0; k < K; ++k) ptr[k + 1] = ptr[k] + (int)v[k].size();
+    for (int k = 0; k < K; ++k) ent.insert(ent.end(), v[k].begin(), v[k].end());
+  };
+  std::vector<int> sp_ptr, tr_ptr, jr_ptr(K + 1, 0);
+  std::vector<int2> sp_ent, tr_ent;
+  std::vector<int4> jr_ent;
+  flatten2(sp, sp_ptr, sp_ent);
+  flatten2(tr, tr_ptr, tr_ent);
+  for (int k = 0; k < K; ++k) jr_ptr[k + 1] = jr_ptr[k] + (int)jr[k].size();
+  for (int k = 0; k < K; ++k) jr_ent.insert(jr_ent.end(), jr[k].begin(), jr[k].end());
+
+  Pool P;
+  const size_t oW = P.add(W.data(), W.size() * 8), oiW = P.add(invW.data(), invW.size() * 8),
+               oN = P.add(nasa.data(), nasa.size() * 8), oA = P.add(arr.data(), arr.size() * 8),
+               oS = P.add(slots.data(), slots.size() * sizeof(int4)), oR = P.add(rev.data(), rev.size() * 4),
+               oF = P.add(fo.data(), fo.size() * 8), oE = P.add(eff.data(), eff.size() * 8),
+               oSp = P.add(sp_ptr.data(), sp_ptr.size() * 4), oSe = P.add(sp_ent.data(), sp_ent.size() * 8),
+               oJp = P.add(jr_ptr.data(), jr_ptr.size() * 4), oJe = P.add(jr_ent.data(), jr_ent.size() * 16),
+               oTp = P.add(tr_ptr.data(), tr_ptr.size() * 4), oTe = P.add(tr_ent.data(), tr_ent.size() * 8);
+  CHEM_CUDA(h, cudaMalloc(&h->d_tables, P.host.size()));
+  CHEM_CUDA(h, cudaMemcpy(h->d_tables, P.host.data(), P.host.size(), cudaMemcpyHostToDevice));
+  unsigned char* b = static_cast<unsigned char*>(h->d_tables);
+  DevMech& m = h->dm;
+  m.K = K;
+  m.I = I;
+  m.n_tb = n_tb;
+  m.n_fo = n_fo;
+  m.i_tb0 = i_tb0;
+  m.i_fo0 = i_fo0;
+  m.i_troe0 = i_troe0;
+  m.W = reinterpret_cast<const double*>(b + oW);
+  m.invW = reinterpret_cast<const double*>(b + oiW);
+  m.nasa = reinterpret_cast<const double*>(b + oN);
+  m.arr = reinterpret_cast<const double*>(b + oA);
+  m.slots = reinterpret_cast<const int4*>(b + oS);
+  m.rev = reinterpret_cast<const int*>(b + oR);
+  m.fo = reinterpret_cast<const double*>(b + oF);
+  m.eff = reinterpret_cast<const double*>(b + oE);
+  m.sp_ptr = reinterpret_cast<const int*>(b + oSp);
+  m.sp_ent = reinterpret_cast<const int2*>(b + oSe);
+  m.jr_ptr = reinterpret_cast<const int*>(b + oJp);
+  m.jr_ent = reinterpret_cast<const int4*>(b + oJe);
+  m.tr_ptr = reinterpret_cast<const int*>(b + oTp);
+  m.tr_ent = reinterpret_cast<const int2*>(b + oTe);
+  return CHEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// handle lifecycle
+// ---------------------------------------------------------------------------
+extern "C" chem_status chem_create(const chem_mechanism_desc* desc, chem_handle* out) {
+  if (!desc || !out) {
+    g_create_error = "chem_create: NULL argument";
+    return CHEM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  std::string v = validate(desc);
+  if (!v.empty()) {
+    g_create_error = "chem_create: " + v;
+    return CHEM_ERR_BAD_MECHANISM;
+  }
+  chem_handle h = new chem_handle_s();
+  h->K = desc->n_species;
+  h->I = desc->n_reactions;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e != cudaSuccess) {
+    g_create_error = cuda_msg("chem_create", e);
+    delete h;
+    return CHEM_ERR_CUDA;
+  }
+  chem_status s = build_tables(h, desc);
+  if (s == CHEM_OK) s = chem_internal_alloc(h, &h->d_queue, sizeof(int) * 4);
+  if (s != CHEM_OK) {
+    g_create_error = h->err;
+    chem_destroy(h);
+    return s;
+  }
+  *out = h;
+  return CHEM_OK;
+}
+
+extern "C" chem_status chem_destroy(chem_handle h) {
+  if (!h) return CHEM_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  chem_internal_release_learned(h);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (void* p : h->allocations) cudaFree(p);
+  if (h->d_tables) cudaFree(h->d_tables);
+  delete h;
+  return CHEM_OK;
+}
+
+chem_status chem_internal_alloc(chem_handle h, void* pp, size_t bytes) {
+  void** p = reinterpret_cast<void**>(pp);
+  cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+  if (e != cudaSuccess) {
+    h->err = cuda_msg("cudaMalloc", e);
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? CHEM_ERR_OOM : CHEM_ERR_CUDA;
+  }
+  h->allocations.push_back(*p);
+  return CHEM_OK;
+}
+
+static void release(chem_handle h, void* p) {
+  if (!p) return;
+  auto it = std::find(h->allocations.begin(), h->allocations.end(), p);
+  if (it != h->allocations.end()) h->allocations.erase(it);
+  cudaFree(p);
+}
+
+// Per-cell statistics buffers sized for n cells.
+static chem_status ensure_stats(chem_handle h, int64_t n) {
+  if (n <= h->stats_cap) return CHEM_OK;
+  cudaDeviceSynchronize();
+  release(h, h->d_sub);
+  release(h, h->d_rej);
+  release(h, h->d_status);
+  release(h, h->d_hfirst);
+  release(h, h->d_cost);
+  h->d_sub = h->d_rej = h->d_status = nullptr;
+  h->d_hfirst = nullptr;
+  h->d_cost = nullptr;
+  h->stats_cap = 0;
+  const int64_t cap = std::max<int64_t>(n, 1024);
+  chem_status s;
+  if ((s = chem_internal_alloc(h, &h->d_sub, cap * 4)) != CHEM_OK) return s;
+  if ((s = chem_internal_alloc(h, &h->d_rej, cap * 4)) != CHEM_OK) return s;
+  if ((s = chem_internal_alloc(h, &h->d_status, cap * 4)) != CHEM_OK) return s;
+  if ((s = chem_internal_alloc(h, &h->d_hfirst, cap * 8)) != CHEM_OK) return s;
+  if ((s = chem_internal_alloc(h, &h->d_cost, cap * 4)) != CHEM_OK) return s;
+  h->stats_cap = cap;
+  h->cost_valid = false;
+  return CHEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// options
+// ---------------------------------------------------------------------------
+struct OptionDef {
+  const char* key;
+  int chem_handle_s::*field;
+  double lo, hi;
+};
+static const OptionDef kOptions[] = {
+    {"precision", &chem_handle_s::precision, 0, 2},
+    {"ir_sweeps", &chem_handle_s::ir_sweeps, 0, 3},
+    {"scheduler", &chem_handle_s::scheduler, 0, 2},
+    {"order", &chem_handle_s::order, 0, 2},
+    {"h0", &chem_handle_s::h0mode, 0, 1},
+    {"max_steps", &chem_handle_s::max_steps, 1, 2147483647.0},
+    {"block", &chem_handle_s::block, 64, 256},
+    {"ctas_per_sm", &chem_handle_s::ctas_per_sm, 0, 64},
+    {"graph", &chem_handle_s::graph, 0, 1},
+    {"autotune", &chem_handle_s::autotune, 0, 1},
+};
+
+extern "C" chem_status chem_set_option(chem_handle h, const char* key, double value) {
+  if (!h || !key) return CHEM_ERR_INVALID_ARG;
+  for (const auto& o : kOptions) {
+    if (std::strcmp(o.key, key) != 0) continue;
+    if (!(value >= o.lo && value <= o.hi) || value != std::floor(value)) {
+      h->err = std::string("chem_set_option: value out of range for ") + key;
+      return CHEM_ERR_INVALID_ARG;
+    }
+    if (std::strcmp(key, "block") == 0 && value != 64 && value != 128 && value != 256) {
+      h->err = "chem_set_option: block must be 64, 128 or 256";
+      return CHEM_ERR_INVALID_ARG;
+    }
+    h->*(o.field) = (int)value;
+    if (std::strcmp(key, "block") == 0) h->autotuned_key = -1;  // explicit choice wins
+    return CHEM_OK;
+  }
+  h->err = std::string("chem_set_option: unknown key ") + key;
+  return CHEM_ERR_INVALID_ARG;
+}
+
+extern "C" chem_status chem_get_option(chem_handle h, const char* key, double* value) {
+  if (!h || !key || !value) return CHEM_ERR_INVALID_ARG;
+  for (const auto& o : kOptions)
+    if (std::strcmp(o.key, key) == 0) {
+      *value = (double)(h->*(o.field));
+      return CHEM_OK;
+    }
+  h->err = std::string("chem_get_option: unknown key ") + key;
+  return CHEM_ERR_INVALID_ARG;
+}
+
+extern "C" const char* chem_last_error(chem_handle h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+extern "C" int32_t chem_n_species(chem_handle h) { return h ? h->K : -1; }
+extern "C" int32_t chem_n_reactions(chem_handle h) { return h ? h->I : -1; }
+
+// ---------------------------------------------------------------------------
+// integration
+// ---------------------------------------------------------------------------
+static bool bad_tol(double dt, double rtol, double atol) {
+  return !(dt > 0.0) || !std::isfinite(dt) || !(rtol > 0.0) || !std::isfinite(rtol) || !(atol >= 0.0) ||
+         !std::isfinite(atol);
+}
+
+chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double dt, double rtol,
+                                    double atol, cudaStream_t st) {
+  chem_handle h0 = jobs[0].h;
+  IntegrateArgs a;
+  std::memset(&a, 0, sizeof a);
+  int64_t total = 0;
+  int Kmax = 0, Imax = 0;
+  for (int j = 0; j < n_jobs; ++j) {
+    chem_handle h = jobs[j].h;
+    chem_status s = ensure_stats(h, jobs[j].n_cells);
+    if (s != CHEM_OK) {
+      h0->err = h->err;
+      return s;
+    }
+    Job& J = a.jobs[j];
+    J.m = h->dm;
+    J.n_cells = jobs[j].n_cells;
+    J.offset = total;
+    J.T = jobs[j].T;
+    J.p = jobs[j].p;
+    J.Y = jobs[j].Y;
+    J.st.substeps = h->d_sub;
+    J.st.rejects = h->d_rej;
+    J.st.h_first = h->d_hfirst;
+    J.st.status = h->d_status;
+    J.cost_out = h->d_cost;
+    J.h0 = nullptr;
+    h->last_n = jobs[j].n_cells;
+    total += jobs[j].n_cells;
+    Kmax = std::max(Kmax, h->K);
+    Imax = std::max(Imax, h->I);
+  }
+  if (total == 0) return CHEM_OK;
+  if (total > 2147483647LL) {
+    h0->err = "chem_integrate: more than 2^31-1 cells in one call";
+    return CHEM_ERR_INVALID_ARG;
+  }
+  a.n_jobs = n_jobs;
+  a.n_total = total;
+  a.dt = dt;
+  a.rtol = rtol;
+  a.atol = atol;
+  a.max_steps = h0->max_steps;
+  a.sched = h0->scheduler;
+  a.ir_sweeps = h0->ir_sweeps;
+  a.smem_K = Kmax;
+  a.smem_I = std::max(Imax, 1);
+  a.queue = static_cast<int*>(h0->d_queue);
+  a.perm = nullptr;
+  chem_status s = chem_internal_prepare_learned(h0, jobs, n_jobs, &a, st);
+  if (s != CHEM_OK) return s;
+  const size_t smem = smem_bytes(a.smem_K, a.smem_I, h0->precision);
+  if (smem > 227 * 1024) {
+    h0->err = "chem_integrate: mechanism too large for shared memory";
+    return CHEM_ERR_INVALID_ARG;
+  }
+  int block = h0->block;
+  if (h0->autotune) {
+    s = chem_internal_autotune(h0, a, st, &block);
+    if (s != CHEM_OK) return s;
+  }
+  int grid;
+  if (a.sched == SCHED_PLAIN) {
+    grid = (int)total;
+  } else {
+    int occ = 0;
+    CHEM_CUDA(h0, occupancy_integrate(block, h0->precision, a.smem_K, a.smem_I, &occ));
+    if (occ < 1) {
+      h0->err = "chem_integrate: kernel does not fit on an SM";
+      return CHEM_ERR_CUDA;
+    }
+    if (h0->ctas_per_sm > 0) occ = std::min(occ, h0->ctas_per_sm);
+    grid = (int)std::min<int64_t>(total, (int64_t)occ * h0->num_sms);
+  }
+  s = chem_internal_launch(h0, a, block, grid, st);
+  if (s != CHEM_OK) return s;
+  for (int j = 0; j < n_jobs; ++j) {
+    jobs[j].h->cost_valid = true;
+    jobs[j].h->cost_n = jobs[j].n_cells;
+  }
+  return CHEM_OK;
+}
+
+// Launch (optionally through a cached CUDA graph).
+chem_status chem_internal_launch(chem_handle h, const IntegrateArgs& a, int block, int grid, cudaStream_t st) {
+  if (h->graph) return chem_internal_graph_launch(h, a, block, grid, st);
+  if (a.sched == SCHED_QUEUE) CHEM_CUDA(h, cudaMemsetAsync(a.queue, 0, sizeof(int), st));
+  CHEM_CUDA(h, launch_integrate(a, block, h->precision, grid, st));
+  return CHEM_OK;
+}
+
+extern "C" chem_status chem_integrate(chem_handle h, int64_t n_cells, double* T, const double* p, double* Y,
+                                      double dt, double rtol, double atol, void* stream) {
+  if (!h) return CHEM_ERR_INVALID_ARG;
+  if (n_cells < 0 || (n_cells > 0 && (!T || !p || !Y)) || bad_tol(dt, rtol, atol)) {
+    h->err = "chem_integrate: invalid argument (n_cells < 0, NULL array, or dt/rtol/atol out of range)";
+    return CHEM_ERR_INVALID_ARG;
+  }
+  chem_job j{h, n_cells, T, p, Y};
+  return chem_internal_integrate(&j, 1, dt, rtol, atol, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" chem_status chem_integrate_jobs(const chem_job* jobs, int32_t n_jobs, double dt, double rtol,
+                                           double atol, void* stream) {
+  if (!jobs || n_jobs < 1 || n_jobs > kMaxJobs || !jobs[0].h) return CHEM_ERR_INVALID_ARG;
+  chem_handle h0 = jobs[0].h;
+  if (bad_tol(dt, rtol, atol)) {
+    h0->err = "chem_integrate_jobs: dt/rtol/atol out of range";
+    return CHEM_ERR_INVALID_ARG;
+  }
+  for (int j = 0; j < n_jobs; ++j) {
+    if (!jobs[j].h || jobs[j].n_cells < 0 || (jobs[j].n_cells > 0 && (!jobs[j].T || !jobs[j].p || !jobs[j].Y))) {
+      h0->err = "chem_integrate_jobs: invalid job";
+      return CHEM_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < j; ++i)
+      if (jobs[i].h == jobs[j].h) {
+        h0->err = "chem_integrate_jobs: each job needs its own handle";
+        return CHEM_ERR_INVALID_ARG;
+      }
+  }
+  return chem_internal_integrate(jobs, n_jobs, dt, rtol, atol, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" chem_status chem_integrate_host(chem_handle h, int64_t n_cells, double* T, const double* p,
+                                           double* Y, double dt, double rtol, double atol, void* stream) {
+  if (!h) return CHEM_ERR_INVALID_ARG;
+  if (n_cells < 0 || (n_cells > 0 && (!T || !p || !Y)) || bad_tol(dt, rtol, atol)) {
+    h->err = "chem_integrate_host: invalid argument";
+    return CHEM_ERR_INVALID_ARG;
+  }
+  if (n_cells == 0) return CHEM_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (n_cells > h->stage_cap) {
+    CHEM_CUDA(h, cudaStreamSynchronize(st));
+    release(h, h->d_stage);
+    h->d_stage = nullptr;
+    h->stage_cap = 0;
+    chem_status s = chem_internal_alloc(h, &h->d_stage, (size_t)n_cells * (h->K + 2) * sizeof(double));
+    if (s != CHEM_OK) return s;
+    h->stage_cap = n_cells;
+  }
+  double* dT = static_cast<double*>(h->d_stage);
+  double* dp = dT + n_cells;
+  double* dY = dp + n_cells;
+  const size_t nY = (size_t)n_cells * h->K * sizeof(double);
+  CHEM_CUDA(h, cudaMemcpyAsync(dT, T, n_cells * sizeof(double), cudaMemcpyHostToDevice, st));
+  CHEM_CUDA(h, cudaMemcpyAsync(dp, p, n_cells * sizeof(double), cudaMemcpyHostToDevice, st));
+  CHEM_CUDA(h, cudaMemcpyAsync(dY, Y, nY, cudaMemcpyHostToDevice, st));
+  chem_status s = chem_integrate(h, n_cells, dT, dp, dY, dt, rtol, atol, stream);
+  if (s != CHEM_OK) return s;
+  CHEM_CUDA(h, cudaMemcpyAsync(T, dT, n_cells * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CHEM_CUDA(h, cudaMemcpyAsync(Y, dY, nY, cudaMemcpyDeviceToHost, st));
+  CHEM_CUDA(h, cudaStreamSynchronize(st));
+  return CHEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// statistics
+// ---------------------------------------------------------------------------
+extern "C" chem_status chem_get_stats(chem_handle h, void* stream, int32_t* substeps, int32_t* rejects,
+                                      double* h_first, int32_t* cell_status) {
+  if (!h) return CHEM_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t n = h->last_n;
+  if (n == 0) return CHEM_OK;
+  if (substeps) CHEM_CUDA(h, cudaMemcpyAsync(substeps, h->d_sub, n * 4, cudaMemcpyDeviceToDevice, st));
+  if (rejects) CHEM_CUDA(h, cudaMemcpyAsync(rejects, h->d_rej, n * 4, cudaMemcpyDeviceToDevice, st));
+  if (h_first) CHEM_CUDA(h, cudaMemcpyAsync(h_first, h->d_hfirst, n * 8, cudaMemcpyDeviceToDevice, st));
+  if (cell_status) CHEM_CUDA(h, cudaMemcpyAsync(cell_status, h->d_status, n * 4, cudaMemcpyDeviceToDevice, st));
+  std::vector<int32_t> hs(n);
+  CHEM_CUDA(h, cudaMemcpyAsync(hs.data(), h->d_status, n * 4, cudaMemcpyDeviceToHost, st));
+  CHEM_CUDA(h, cudaStreamSynchronize(st));
+  for (int64_t i = 0; i < n; ++i)
+    if (hs[i] != CHEM_CELL_OK) {
+      h->err = "chem_get_stats: some cells failed (see cell_status)";
+      return CHEM_ERR_CELLS_FAILED;
+    }
+  return CHEM_OK;
+}
+
+extern "C" chem_status chem_get_totals(chem_handle h, void* stream, int64_t* n_cells, int64_t* substeps,
+                                       int64_t* rejects, int64_t* failed) {
+  if (!h) return CHEM_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t n = h->last_n;
+  std::vector<int32_t> a(n), b(n), c(n);
+  if (n > 0) {
+    CHEM_CUDA(h, cudaMemcpyAsync(a.data(), h->d_sub, n * 4, cudaMemcpyDeviceToHost, st));
+    CHEM_CUDA(h, cudaMemcpyAsync(b.data(), h->d_rej, n * 4, cudaMemcpyDeviceToHost, st));
+    CHEM_CUDA(h, cudaMemcpyAsync(c.data(), h->d_status, n * 4, cudaMemcpyDeviceToHost, st));
+  }
+  CHEM_CUDA(h, cudaStreamSynchronize(st));
+  int64_t s1 = 0, s2 = 0, s3 = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    s1 += a[i];
+    s2 += b[i];
+    s3 += c[i] != CHEM_CELL_OK;
+  }
+  if (n_cells) *n_cells = n;
+  if (substeps) *substeps = s1;
+  if (rejects) *rejects = s2;
+  if (failed) *failed = s3;
+  return CHEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// diagnostics
+// ---------------------------------------------------------------------------
+extern "C" chem_status chem_eval_rhs(chem_handle h, int64_t n, const double* T, const double* p,
+                                     const double* Y, double* f, void* stream) {
+  if (!h || n < 0 || (n > 0 && (!T || !p || !Y || !f))) return CHEM_ERR_INVALID_ARG;
+  if (n == 0) return CHEM_OK;
+  CHEM_CUDA(h, launch_diag(h->dm, n, T, p, Y, f, 0, 0, 0, 0, PREC_FP64, static_cast<cudaStream_t>(stream)));
+  return CHEM_OK;
+}
+
+extern "C" chem_status chem_eval_jacobian(chem_handle h, int64_t n, const double* T, const double* p,
+                                          const double* Y, double* J, void* stream) {
+  if (!h || n < 0 || (n > 0 && (!T || !p || !Y || !J))) return CHEM_ERR_INVALID_ARG;
+  if (n == 0) return CHEM_OK;
+  CHEM_CUDA(h, launch_diag(h->dm, n, T, p, Y, J, 0, 0, 0, 1, h->precision, static_cast<cudaStream_t>(stream)));
+  return CHEM_OK;
+}
+
+extern "C" chem_status chem_eval_h0(chem_handle h, int64_t n, const double* T, const double* p, const double* Y,
+                                    double dt, double rtol, double atol, double* h0, void* stream) {
+  if (!h || n < 0 || (n > 0 && (!T || !p || !Y || !h0)) || bad_tol(dt, rtol, atol)) return CHEM_ERR_INVALID_ARG;
+  if (n == 0) return CHEM_OK;
+  CHEM_CUDA(h, launch_diag(h->dm, n, T, p, Y, h0, dt, rtol, atol, 2, PREC_FP64, static_cast<cudaStream_t>(stream)));
+  return CHEM_OK;
+}
+
+extern "C" chem_status chem_lu_solve_batched(int64_t n_mat, int32_t dim, const double* A, const double* b,
+                                             double* x, int32_t* info, int32_t precision, int32_t ir_sweeps,
+                                             void* stream) {
+  if (n_mat < 0 || dim < 1 || dim > 128 || precision < 0 || precision > 2 || ir_sweeps < 0 || ir_sweeps > 3)
+    return CHEM_ERR_INVALID_ARG;
+  if (n_mat == 0) return CHEM_OK;
+  if (!A || !b || !x) return CHEM_ERR_INVALID_ARG;
+  cudaError_t e = launch_lu_solve(n_mat, dim, A, b, x, info, precision, ir_sweeps, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? CHEM_OK : CHEM_ERR_CUDA;
+}
+
+extern "C" void chem_rosenbrock_tableau(double* gamma, double* a, double* c, double* m, double* e) {
+  if (gamma) *gamma = kRodasGamma;
+  for (int i = 0; i < 6; ++i) {
+    for (int j = 0; j < 6; ++j) {
+      if (a) a[6 * i + j] = kRodasA[i][j];
+      if (c) c[6 * i + j] = kRodasC[i][j];
+    }
+    if (m) m[i] = kRodasM[i];
+    if (e) e[i] = kRodasE[i];
+  }
+}

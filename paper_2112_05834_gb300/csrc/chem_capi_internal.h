@@ -1,0 +1,74 @@
+// Handle definition and internal hooks shared by the host translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "chem.h"
+#include "chem_internal.h"
+
+struct chem_mlp_s;
+
+struct chem_handle_s {
+  int device = 0;
+  int num_sms = 1;
+  int K = 0, I = 0;
+  chem::DevMech dm{};
+  void* d_tables = nullptr;
+  std::vector<int> rxn_order;       // sorted reaction position -> caller's reaction index
+  std::vector<void*> allocations;   // every other device allocation of the handle
+  // options
+  int precision = chem::PREC_FP64;
+  int ir_sweeps = 2;
+  int scheduler = chem::SCHED_QUEUE;
+  int order = 0;
+  int h0mode = 0;
+  int max_steps = 100000;
+  int block = 128;
+  int ctas_per_sm = 0;
+  int graph = 0;
+  int autotune = 0;
+  // per-cell statistics of the last call
+  int64_t stats_cap = 0;
+  int64_t last_n = 0;
+  int32_t* d_sub = nullptr;
+  int32_t* d_rej = nullptr;
+  int32_t* d_status = nullptr;
+  double* d_hfirst = nullptr;
+  float* d_cost = nullptr;  // substeps of the last call, for cost ordering
+  bool cost_valid = false;
+  int64_t cost_n = 0;
+  void* d_queue = nullptr;
+  // staging buffers of chem_integrate_host
+  void* d_stage = nullptr;
+  int64_t stage_cap = 0;
+  // learned scheduling / initial step
+  chem_mlp_s* mlp = nullptr;        // model attached with chem_mlp_attach (not owned)
+  void* d_order = nullptr;          // permutation + sort scratch
+  int64_t order_cap = 0;
+  void* d_h0 = nullptr;             // predicted initial steps
+  int64_t h0_cap = 0;
+  // CUDA graph cache
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<unsigned char> gkey;
+  // autotuner cache: key -> block
+  long long autotuned_key = -1;
+  int autotuned_block = 128;
+  std::string err;
+};
+
+chem_status chem_internal_alloc(chem_handle h, void* pp, size_t bytes);
+chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double dt, double rtol, double atol,
+                                    cudaStream_t st);
+chem_status chem_internal_launch(chem_handle h, const chem::IntegrateArgs& a, int block, int grid,
+                                 cudaStream_t st);
+chem_status chem_internal_graph_launch(chem_handle h, const chem::IntegrateArgs& a, int block, int grid,
+                                       cudaStream_t st);
+chem_status chem_internal_autotune(chem_handle h, const chem::IntegrateArgs& a, cudaStream_t st, int* block);
+chem_status chem_internal_prepare_learned(chem_handle h, const chem_job* jobs, int32_t n_jobs,
+                                          chem::IntegrateArgs* a, cudaStream_t st);
+void chem_internal_release_learned(chem_handle h);

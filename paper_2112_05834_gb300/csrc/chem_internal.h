@@ -1,0 +1,88 @@
+// Internal structures shared by the host C-ABI and the device kernels.
+#pragma once
+
+#include <vector_types.h>
+
+#include <cstdint>
+
+namespace chem {
+
+constexpr int kMaxJobs = 8;
+constexpr double kRc = 8.31446261815324e7;  // erg / (mol K)
+constexpr double kP0 = 1.01325e6;           // dyn / cm^2, standard state (1 atm)
+constexpr double kTmin = 200.0, kTmax = 6000.0;
+
+// FP64: everything in FP64.
+// MIXED: Jacobian assembled in FP64 (kept for the refinement residual), LU and
+//        triangular solves in FP32, FP64 iterative refinement of every solve.
+// FP32ASM: Jacobian assembled in FP32 as well; refinement residual against the
+//        FP32-assembled matrix (kept for comparison: it perturbs the method).
+enum Precision { PREC_FP64 = 0, PREC_MIXED = 1, PREC_FP32ASM = 2 };
+enum Sched { SCHED_PLAIN = 0, SCHED_STATIC = 1, SCHED_QUEUE = 2 };
+
+// Reaction kinds after the host sorts reactions by kind (warp-uniform branches).
+enum RxnKind { RK_ELEM = 0, RK_TB = 1, RK_LIND = 2, RK_TROE = 3 };
+
+// Device-resident struct-of-arrays tables of one mechanism. Reactions are stored
+// sorted by kind; species keep the caller's order.
+struct DevMech {
+  int K, I;
+  int n_tb;   // reactions with a third-body concentration (kinds 1..3)
+  int n_fo;   // falloff reactions (kinds 2, 3)
+  int i_tb0;  // first reaction of kind >= 1 (sorted order)
+  int i_fo0;  // first reaction of kind >= 2
+  int i_troe0;  // first reaction of kind 3
+  const double* W;      // [K]
+  const double* invW;   // [K]
+  const double* nasa;   // [K][36]: for range r (0 below T_mid, 1 above) at 17 r:
+                        //   cp/R coefficients a1..a5, H/RT coefficients a1, a2/2, a3/3,
+                        //   a4/4, a5/5, a6, S/R coefficients a1, a2, a3/2, a4/3, a5/4, a7;
+                        //   [34] = T_mid
+  const double* arr;    // [I][4]: ln A, b, Ea_R, dnu
+  const int4* slots;    // [I]: reactant slot 0/1, product slot 0/1 species (-1 empty);
+                        //      a coefficient of 2 appears as two equal slots
+  const int* rev;       // [I] 0/1
+  const double* fo;     // [n_fo][8]: ln A0, b0, Ea0_R, alpha, T***, T*, T**, 0
+  const double* eff;    // [n_tb][K] (row r belongs to reaction i_tb0 + r)
+  const int* sp_ptr;    // [K+1] species -> (reaction, nu) CSR
+  const int2* sp_ent;
+  const int* jr_ptr;    // [K+1] Jacobian row k -> (col j, reaction i, nu_ki, slot)
+  const int4* jr_ent;
+  const int* tr_ptr;    // [K+1] row k -> (reaction i with [M], nu_ki)
+  const int2* tr_ent;
+};
+
+struct CellStats {
+  int32_t* substeps;
+  int32_t* rejects;
+  double* h_first;
+  int32_t* status;
+};
+
+struct Job {
+  DevMech m;
+  int64_t n_cells;
+  int64_t offset;  // first global work index of this job
+  double* T;
+  const double* p;
+  double* Y;
+  CellStats st;
+  const double* h0;   // optional per-cell initial step (learned), may be null
+  float* cost_out;    // optional per-cell cost (substeps) for the next call's ordering
+};
+
+struct IntegrateArgs {
+  Job jobs[kMaxJobs];
+  int n_jobs;
+  int64_t n_total;
+  const int* perm;     // optional order of global work indices (queue/plain)
+  int* queue;          // device counter (queue scheduler)
+  double dt, rtol, atol;
+  int max_steps;
+  int sched;
+  int ir_sweeps;
+  int use_h0;          // 1: take jobs[j].h0 when finite and positive
+  int smem_K, smem_I;  // sizes the shared-memory carve-up was computed for
+};
+
+}  // namespace chem

@@ -1,0 +1,1022 @@
+// Device code of the batched stiff-chemistry integrator (sm_103a).
+//
+// One CTA integrates one cell at a time; its warps share the cell's work:
+// species and reactions are strided over threads for the rates, Jacobian rows
+// and columns over warps/lanes for the assembly, rows over warps for the LU
+// trailing update, and one warp runs the triangular solves. All per-cell data
+// (state, stage vectors, per-reaction derivative data, the iteration matrix)
+// lives in shared memory; the mechanism tables are read through the L1 cache.
+//
+// Paper mapping: rates and RHS = pyJac's reaction-rate evaluation; analytic
+// Jacobian = pyJac's Jacobian (Methodology, "Analytical Jacobian and improved ODE
+// solution"); LU + substitution = the LAPACK replacement of OpenFOAM's linear
+// algebra (same section); the per-cell loop = the implicit ODE solver of the
+// Introduction; the work queue = DLBFoam's redistribution of cell problems
+// (Methodology, "DLBFoam: Dynamic load balancing"), reinterpreted inside one GPU.
+
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cmath>
+#include <cstdint>
+#include <type_traits>
+
+#include "chem.h"
+#include "chem_internal.h"
+#include "chem_kernels.h"
+#include "rodas4.h"
+
+namespace chem {
+
+#define FULLMASK 0xffffffffu
+
+// Rosenbrock coefficients in constant memory (stages are indexed at run time).
+__constant__ double c_rodasA[6][6] = CHEM_RODAS_A;
+__constant__ double c_rodasC[6][6] = CHEM_RODAS_C;
+__constant__ double c_rodasM[6] = CHEM_RODAS_M;
+
+// Precision policy: LU = type of the factorised matrix, ASM = type the Jacobian is
+// assembled in; IR = refine each solve against the assembled matrix.
+template <int PREC>
+struct Policy {
+  using LU = double;
+  using ASM = double;
+  static constexpr bool IR = false;
+};
+template <>
+struct Policy<PREC_MIXED> {
+  using LU = float;
+  using ASM = double;
+  static constexpr bool IR = true;
+};
+template <>
+struct Policy<PREC_FP32ASM> {
+  using LU = float;
+  using ASM = float;
+  static constexpr bool IR = true;
+};
+
+// ---------------------------------------------------------------------------
+// shared-memory carve-up
+// ---------------------------------------------------------------------------
+struct Layout {
+  int nmax, ld;            // matrix dimension bound and leading dimension (odd)
+  int Kmax, Imax;
+  size_t off_vec, off_sp, off_rx, off_M, off_M0, off_piv, off_red, total;
+};
+
+__host__ __device__ inline int odd_ld(int n) { return n | 1; }
+
+// vectors (double): y, yn, ys, f0, fv, rr, u[6], sc  -> 13 n
+// species (double): C, hRT, cpR, eg, dcp, dk, akT, ek -> 8 K
+// reactions (double): q, D, dTc, P, dqs[4] -> 8 I
+__host__ __device__ inline Layout make_layout(int Kmax, int Imax, int prec) {
+  Layout L;
+  L.nmax = Kmax + 1;
+  L.ld = odd_ld(L.nmax);
+  L.Kmax = Kmax;
+  L.Imax = Imax;
+  size_t o = 0;
+  L.off_red = o;
+  o += 64 * sizeof(double);
+  L.off_vec = o;
+  o += (size_t)13 * L.nmax * sizeof(double);
+  L.off_sp = o;
+  o += (size_t)8 * Kmax * sizeof(double);
+  L.off_rx = o;
+  o += (size_t)8 * Imax * sizeof(double);
+  const size_t es = prec == PREC_FP64 ? sizeof(double) : sizeof(float);
+  L.off_M = o;
+  o += (size_t)L.nmax * L.ld * es;
+  o = (o + 15) & ~(size_t)15;
+  L.off_M0 = o;
+  if (prec == PREC_MIXED) o += (size_t)L.nmax * L.ld * sizeof(double);
+  if (prec == PREC_FP32ASM) o += (size_t)L.nmax * L.ld * sizeof(float);
+  o = (o + 15) & ~(size_t)15;
+  L.off_piv = o;
+  o += (size_t)2 * L.nmax * sizeof(int);  // pivots, permutation
+  o += (size_t)L.nmax * sizeof(double);   // inverse diagonal of U
+  o = (o + 15) & ~(size_t)15;
+  L.total = o;
+  return L;
+}
+
+size_t smem_bytes(int Kmax, int Imax, int prec) { return make_layout(Kmax, Imax, prec).total; }
+
+// Scalars kept in the reduction area (after the 4 x NW partial-sum slots).
+enum { SC_LOGT = 48, SC_INVP = 49, SC_FLAG = 50, SC_MISC = 51 };
+
+template <int NW>
+struct Cta {
+  static constexpr int NT = NW * 32;
+  int tid, lane, warp;
+  double* red;
+  // vectors
+  double *y, *yn, *ys, *f0, *fv, *rr, *u, *sc;
+  // species
+  double *C, *hRT, *cpR, *eg, *dcp, *dk, *akT, *ek;
+  // reactions
+  double *q, *D, *dTc, *P, *dqs;
+  void* M;
+  void* M0;
+  int *piv, *perm;
+  double* invd;
+
+  __device__ void bind(unsigned char* base, const Layout& L) {
+    tid = threadIdx.x;
+    lane = tid & 31;
+    warp = tid >> 5;
+    red = reinterpret_cast<double*>(base + L.off_red);
+    double* v = reinterpret_cast<double*>(base + L.off_vec);
+    const int n = L.nmax;
+    y = v;
+    yn = v + n;
+    ys = v + 2 * n;
+    f0 = v + 3 * n;
+    fv = v + 4 * n;
+    rr = v + 5 * n;
+    u = v + 6 * n;   // 6 n
+    sc = v + 12 * n;
+    double* s = reinterpret_cast<double*>(base + L.off_sp);
+    const int K = L.Kmax;
+    C = s;
+    hRT = s + K;
+    cpR = s + 2 * K;
+    eg = s + 3 * K;
+    dcp = s + 4 * K;
+    dk = s + 5 * K;
+    akT = s + 6 * K;
+    ek = s + 7 * K;
+    double* r = reinterpret_cast<double*>(base + L.off_rx);
+    const int I = L.Imax;
+    q = r;
+    D = r + I;
+    dTc = r + 2 * I;
+    P = r + 3 * I;
+    dqs = r + 4 * I;
+    M = base + L.off_M;
+    M0 = base + L.off_M0;
+    piv = reinterpret_cast<int*>(base + L.off_piv);
+    perm = piv + L.nmax;
+    invd = reinterpret_cast<double*>(perm + L.nmax);
+  }
+
+  // Sum of NV values over the CTA; every thread receives the same totals
+  // (fixed summation order: deterministic).
+  template <int NV>
+  __device__ void sum(double (&v)[NV]) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      double x = v[a];
+#pragma unroll
+      for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULLMASK, x, o);
+      if (lane == 0) red[a * NW + warp] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      double s = 0.0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) s += red[a * NW + w];
+      v[a] = s;
+    }
+    __syncthreads();
+  }
+};
+
+// Cell-level scalars shared by all threads of the CTA (identical in every thread).
+struct Scal {
+  double T, invT, logT, rho, Wbar, cpm, fT, dcpm, Scpw;
+};
+
+// ---------------------------------------------------------------------------
+// thermo, rates, RHS and the per-reaction Jacobian data
+// ---------------------------------------------------------------------------
+// RHS of y = [T, Y] at constant p into f[0..K]. With JAC, also the data the
+// Jacobian assembly needs: per reaction the slot derivatives dq/dC, dq/dT at
+// fixed C, sum_k C_k dq/dC_k (D), and the third-body/falloff coefficient P of
+// eff_j in dq/dC_j; per species d_k = sum_i nu_ki D_i and a_kT = sum nu dTc.
+template <int NW, bool JAC>
+__device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p, double* f) {
+  constexpr int NT = NW * 32;
+  const int K = m.K, I = m.I;
+  Scal s;
+  s.T = y[0];
+  s.invT = 1.0 / s.T;
+  if (c.warp == 0) {
+    double lg = log(s.T);
+    if (c.lane == 0) c.red[SC_LOGT] = lg;
+  }
+  {
+    double part[1] = {0.0};
+    for (int k = c.tid; k < K; k += NT) part[0] += y[1 + k] * m.invW[k];
+    c.sum(part);
+    s.Wbar = 1.0 / part[0];
+    s.rho = p / (kRc * s.T * part[0]);
+  }
+  s.logT = c.red[SC_LOGT];
+  const double T = s.T, invT = s.invT, logT = s.logT;
+  // species: thermo, exp(G/RT), concentrations
+  for (int k = c.tid; k < K; k += NT) {
+    const double* a = m.nasa + 36 * k;
+    a += (T < a[34]) ? 0 : 17;
+    double cp = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
+    double h = a[5] + T * (a[6] + T * (a[7] + T * (a[8] + T * a[9]))) + a[10] * invT;
+    double sr = a[11] * logT + T * (a[12] + T * (a[13] + T * (a[14] + T * a[15]))) + a[16];
+    c.cpR[k] = cp;
+    c.hRT[k] = h;
+    c.eg[k] = exp(h - sr);
+    c.C[k] = s.rho * y[1 + k] * m.invW[k];
+    if (JAC) c.dcp[k] = a[1] + T * (2.0 * a[2] + T * (3.0 * a[3] + T * 4.0 * a[4]));
+  }
+  __syncthreads();
+  const double cRT = kRc * T / kP0;  // (P0 / (Rc T))^-1
+  for (int i = c.tid; i < I; i += NT) {
+    const double* arp = m.arr + 4 * i;
+    const double2 a01 = reinterpret_cast<const double2*>(arp)[0];
+    const double2 a23 = reinterpret_cast<const double2*>(arp)[1];
+    const struct { double x, y, z, w; } ar = {a01.x, a01.y, a23.x, a23.y};
+    const int4 sl = m.slots[i];
+    double kf = exp(ar.x + ar.y * logT - ar.z * invT);
+    const double Ca = c.C[sl.x];
+    const double Cb = sl.y >= 0 ? c.C[sl.y] : 1.0;
+    const double Cc = c.C[sl.z];
+    const double Cd = sl.w >= 0 ? c.C[sl.w] : 1.0;
+    const double Pf = Ca * Cb, Pb = Cc * Cd;
+    // 1/Kc = exp(dG/RT) (Rc T/P0)^dnu with exp(dG/RT) from the species factors
+    double ratio = 0.0;
+    if (m.rev[i]) {
+      double num = c.eg[sl.z] * (sl.w >= 0 ? c.eg[sl.w] : 1.0);
+      double den = c.eg[sl.x] * (sl.y >= 0 ? c.eg[sl.y] : 1.0);
+      ratio = num / den;
+      if (ar.w > 0.5) ratio *= cRT;
+      else if (ar.w < -0.5) ratio /= cRT;
+    }
+    double Mc = 0.0, phi = 1.0;
+    double dk_dM = 0.0, dlnk = ar.y * invT + ar.z * invT * invT, dk_dT = 0.0;
+    if (i >= m.i_tb0) {
+      const double* e = m.eff + (size_t)(i - m.i_tb0) * K;
+      for (int k = 0; k < K; ++k) Mc += e[k] * c.C[k];
+      if (i < m.i_fo0) phi = Mc;
+    }
+    if (i >= m.i_fo0) {
+      const double* fo = m.fo + 8 * (i - m.i_fo0);
+      const double kinf = kf;
+      const double k0 = exp(fo[0] + fo[1] * logT - fo[2] * invT);
+      const double dlnk0 = fo[1] * invT + fo[2] * invT * invT;
+      const double Pr = k0 * Mc / kinf;
+      double F = 1.0, dF_dPr = 0.0, dF_dT = 0.0;
+      if (i >= m.i_troe0) {
+        const double alpha = fo[3];
+        const double e3 = exp(-T / fo[4]), e1 = exp(-T / fo[5]);
+        double Fc = (1.0 - alpha) * e3 + alpha * e1;
+        double dFc = -(1.0 - alpha) / fo[4] * e3 - alpha / fo[5] * e1;
+        if (fo[6] > 0.0) {
+          const double e2 = exp(-fo[6] * invT);
+          Fc += e2;
+          dFc += fo[6] * invT * invT * e2;
+        }
+        const double lF = log10(Fc);
+        const double cc = -0.4 - 0.67 * lF, nn = 0.75 - 1.27 * lF;
+        const double x = log10(Pr) + cc;
+        const double den = nn - 0.14 * x;
+        const double f1 = x / den;
+        const double g = 1.0 + f1 * f1;
+        const double lgF = lF / g;
+        F = exp10(lgF);
+        if (JAC) {
+          const double ln10 = 2.302585092994046;
+          const double df1_dL = nn / (den * den);
+          const double df1_dlF = (-0.67 * den - x * (-1.27 + 0.14 * 0.67)) / (den * den);
+          const double dlgF_dL = -lF * 2.0 * f1 / (g * g) * df1_dL;
+          const double dlgF_dlF = 1.0 / g - lF * 2.0 * f1 / (g * g) * df1_dlF;
+          dF_dPr = F * dlgF_dL / Pr;
+          dF_dT = F * ln10 * dlgF_dlF * (dFc / (Fc * ln10));
+        }
+      }
+      const double red1 = 1.0 / (1.0 + Pr);
+      kf = kinf * Pr * red1 * F;
+      if (JAC) {
+        const double dPr_dM = k0 / kinf;
+        const double dPr_dT = Pr * (dlnk0 - dlnk);
+        dk_dM = kinf * F * red1 * red1 * dPr_dM + kinf * Pr * red1 * dF_dPr * dPr_dM;
+        dk_dT = kinf * dlnk * Pr * red1 * F + kinf * F * red1 * red1 * dPr_dT +
+                kinf * Pr * red1 * (dF_dT + dF_dPr * dPr_dT);
+      }
+    }
+    const double kr = kf * ratio;
+    const double net = kf * Pf - kr * Pb;
+    c.q[i] = phi * net;
+    if (JAC) {
+      // d ln Kc / dT = dH/(R T^2) - dnu/T
+      double dH = c.hRT[sl.z] + (sl.w >= 0 ? c.hRT[sl.w] : 0.0) - c.hRT[sl.x] -
+                  (sl.y >= 0 ? c.hRT[sl.y] : 0.0);
+      const double dlnKc = (dH - ar.w) * invT;
+      double* dq = c.dqs + 4 * i;
+      dq[0] = phi * kf * Cb;
+      dq[1] = sl.y >= 0 ? phi * kf * Ca : 0.0;
+      dq[2] = -phi * kr * Cd;
+      dq[3] = sl.w >= 0 ? -phi * kr * Cc : 0.0;
+      double Dsum = Ca * dq[0] + (sl.y >= 0 ? Cb * dq[1] : 0.0) + Cc * dq[2] + (sl.w >= 0 ? Cd * dq[3] : 0.0);
+      double dtc, Pc;
+      if (i >= m.i_fo0) {
+        const double netc = Pf - ratio * Pb;
+        dtc = dk_dT * netc + (m.rev[i] ? kr * Pb * dlnKc : 0.0);
+        Pc = dk_dM * netc;
+      } else {
+        const double dkf = kf * dlnk;
+        const double dkr = kr * (dlnk - dlnKc);
+        dtc = phi * (dkf * Pf - dkr * Pb);
+        Pc = (i >= m.i_tb0) ? net : 0.0;
+      }
+      if (i >= m.i_tb0) Dsum += Mc * Pc;
+      c.dTc[i] = dtc;
+      c.P[i] = Pc;
+      c.D[i] = Dsum;
+    }
+  }
+  __syncthreads();
+  // species: production rates, f_k, enthalpy and heat-capacity sums
+  double part[JAC ? 4 : 2];
+  part[0] = part[1] = 0.0;
+  if (JAC) part[2] = part[3] = 0.0;
+  for (int k = c.tid; k < K; k += NT) {
+    double w = 0.0, dd = 0.0, at = 0.0;
+    for (int e = m.sp_ptr[k]; e < m.sp_ptr[k + 1]; ++e) {
+      const int2 en = m.sp_ent[e];
+      const double nu = (double)en.y;
+      w += nu * c.q[en.x];
+      if (JAC) {
+        dd += nu * c.D[en.x];
+        at += nu * c.dTc[en.x];
+      }
+    }
+    f[1 + k] = m.W[k] * w / s.rho;
+    part[0] += c.hRT[k] * w;                  // Qh / (Rc T)
+    part[1] += y[1 + k] * c.cpR[k] * m.invW[k];  // cpm / Rc
+    if (JAC) {
+      c.dk[k] = dd;
+      c.akT[k] = at;
+      part[2] += y[1 + k] * c.dcp[k] * m.invW[k];  // dcpm/dT / Rc
+      part[3] += c.cpR[k] * w;                      // sum cp_k omega_k / Rc
+    }
+  }
+  c.sum(part);
+  s.cpm = kRc * part[1];
+  const double Qh = kRc * T * part[0];
+  s.fT = -Qh / (s.rho * s.cpm);
+  if (JAC) {
+    s.dcpm = kRc * part[2];
+    s.Scpw = kRc * part[3];
+  }
+  if (c.tid == 0) f[0] = s.fT;
+  __syncthreads();
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Jacobian assembly (precision R) from the data of eval_rhs<JAC=true>.
+// Writes J (jac_only) or the iteration matrix M = I/(h gamma) - J into c.M.
+// ---------------------------------------------------------------------------
+template <int NW, class R>
+__device__ void assemble(const DevMech& m, Cta<NW>& c, const Scal& s, const double* y, const double* f,
+                         double fac, bool jac_only, void* target) {
+  constexpr int NT = NW * 32;
+  const int K = m.K, n = K + 1, ld = odd_ld(n);
+  R* A = reinterpret_cast<R*>(target);
+  // e_k = h_k / (W_k cp) with the molar enthalpy h_k = hRT_k Rc T
+  for (int k = c.tid; k < K; k += NT) c.ek[k] = c.hRT[k] * kRc * s.T * m.invW[k] / s.cpm;
+  // (1) dense third-body / falloff part of A_kj = sum_i nu_ki dq_i/dC_j
+  for (int k = c.warp; k < K; k += NW) {
+    const int t0 = m.tr_ptr[k], t1 = m.tr_ptr[k + 1];
+    for (int j = c.lane; j < K; j += 32) {
+      R a = R(0);
+      for (int t = t0; t < t1; ++t) {
+        const int2 en = m.tr_ent[t];
+        a += R(en.y) * R(c.P[en.x]) * R(m.eff[(size_t)(en.x - m.i_tb0) * K + j]);
+      }
+      A[(1 + k) * ld + 1 + j] = a;
+    }
+  }
+  __syncthreads();
+  // (2) sparse mass-action part, one thread per row
+  for (int k = c.tid; k < K; k += NT) {
+    R* row = A + (1 + k) * ld + 1;
+    for (int e = m.jr_ptr[k]; e < m.jr_ptr[k + 1]; ++e) {
+      const int4 en = m.jr_ent[e];
+      row[en.x] += R(en.z) * R(c.dqs[4 * en.y + en.w]);
+    }
+  }
+  __syncthreads();
+  // (3) species block and T column:
+  //   J_kj = (W_k/W_j) (A_kj - (Wbar/rho) d_k) + f_k Wbar / W_j
+  //   J_k0 = (W_k/rho) (a_kT - d_k / T) + f_k / T
+  const R wr = R(s.Wbar / s.rho), wb = R(s.Wbar);
+  for (int k = c.warp; k < K; k += NW) {
+    const R Wk = R(m.W[k]), dk = R(c.dk[k]), fk = R(f[1 + k]);
+    R* row = A + (1 + k) * ld + 1;
+    for (int j = c.lane; j < K; j += 32) {
+      const R iW = R(m.invW[j]);
+      row[j] = Wk * iW * (row[j] - wr * dk) + fk * wb * iW;
+    }
+    if (c.lane == 0)
+      A[(1 + k) * ld] = R(m.W[k] / s.rho * (c.akT[k] - c.dk[k] * s.invT) + f[1 + k] * s.invT);
+  }
+  __syncthreads();
+  // (4) temperature row: J_0j = -sum_k e_k J_kj - f_T cp_j / (W_j cp);
+  //     J_00 = -sum_k e_k J_k0 - sum_k cp_k omega_k / (rho cp) - f_T cp'/cp
+  for (int j = c.tid; j < n; j += NT) {
+    R acc = R(0);
+    for (int k = 0; k < K; ++k) acc += R(c.ek[k]) * A[(1 + k) * ld + j];
+    R extra;
+    if (j == 0)
+      extra = R(s.Scpw / (s.rho * s.cpm) + s.fT * s.dcpm / s.cpm);
+    else
+      extra = R(s.fT * c.cpR[j - 1] * kRc * m.invW[j - 1] / s.cpm);
+    A[j] = -acc - extra;
+  }
+  __syncthreads();
+  if (jac_only) return;
+  // (5) M = I/(h gamma) - J
+  const R rf = R(fac);
+  for (int i = c.warp; i < n; i += NW)
+    for (int j = c.lane; j < n; j += 32) {
+      R v = -A[i * ld + j];
+      if (i == j) v += rf;
+      A[i * ld + j] = v;
+    }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// dense LU with partial pivoting (row interchanges to the largest |a_ik|, lowest
+// row index on ties), in place; then the composed row permutation and the inverse
+// diagonal of U for the solves. Returns 0 or 1 + k for a zero pivot at column k.
+// ---------------------------------------------------------------------------
+template <int NW, class R>
+__device__ int lu_factor(Cta<NW>& c, R* a, int n) {
+  constexpr int NT = NW * 32;
+  const int ld = odd_ld(n);
+  int info = 0;
+  for (int k = 0; k < n; ++k) {
+    if (c.warp == 0) {
+      double best = -1.0;
+      int bi = n;
+      for (int i = k + c.lane; i < n; i += 32) {
+        const double v = fabs((double)a[i * ld + k]);
+        if (v > best) { best = v; bi = i; }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const double ov = __shfl_xor_sync(FULLMASK, best, o);
+        const int oi = __shfl_xor_sync(FULLMASK, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (c.lane == 0) {
+        if (bi >= n) {  // the whole column is NaN: report a zero pivot, keep k
+          bi = k;
+          best = 0.0;
+        }
+        c.piv[k] = bi;
+        c.red[SC_INVP] = best > 0.0 ? 1.0 / (double)a[bi * ld + k] : 0.0;
+      }
+    }
+    __syncthreads();
+    const int p = c.piv[k];
+    const R invp = R(c.red[SC_INVP]);
+    if (invp == R(0) && info == 0) info = k + 1;
+    if (p != k)
+      for (int j = c.tid; j < n; j += NT) {
+        const R t = a[k * ld + j];
+        a[k * ld + j] = a[p * ld + j];
+        a[p * ld + j] = t;
+      }
+    __syncthreads();
+    for (int i = k + 1 + c.warp; i < n; i += NW) {
+      const R l = a[i * ld + k] * invp;
+      __syncwarp();
+      if (c.lane == 0) a[i * ld + k] = l;
+      for (int j = k + 1 + c.lane; j < n; j += 32) a[i * ld + j] -= l * a[k * ld + j];
+    }
+    __syncthreads();
+  }
+  // composed permutation: position i of the pivoted system holds original row perm[i]
+  if (c.tid == 0) {
+    for (int i = 0; i < n; ++i) c.perm[i] = i;
+    for (int k = 0; k < n; ++k) {
+      const int p = c.piv[k];
+      const int t = c.perm[k];
+      c.perm[k] = c.perm[p];
+      c.perm[p] = t;
+    }
+  }
+  for (int i = c.tid; i < n; i += NT) c.invd[i] = 1.0 / (double)a[i * ld + i];
+  __syncthreads();
+  return info;
+}
+
+// Forward/back substitution by one warp, in place on x (already permuted).
+template <class R>
+__device__ void lu_solve_warp(const R* a, int n, const double* invd, R* x, int lane) {
+  const int ld = odd_ld(n);
+  for (int i0 = 0; i0 < n; i0 += 32) {
+    const int i = i0 + lane;
+    const int jend = min(i0 + 32, n);
+    R xi = i < n ? x[i] : R(0);
+    for (int j = i0; j < jend; ++j) {
+      const R xj = __shfl_sync(FULLMASK, xi, j - i0);
+      if (i > j && i < n) xi -= a[i * ld + j] * xj;
+    }
+    if (i < n) x[i] = xi;
+    __syncwarp();
+    for (int r = i0 + 32 + lane; r < n; r += 32) {
+      R sacc = R(0);
+      for (int j = i0; j < jend; ++j) sacc += a[r * ld + j] * x[j];
+      x[r] -= sacc;
+    }
+    __syncwarp();
+  }
+  for (int i1 = n; i1 > 0; i1 -= 32) {
+    const int i0 = max(0, i1 - 32);
+    const int i = i0 + lane;
+    R xi = i < i1 ? x[i] : R(0);
+    for (int j = i1 - 1; j >= i0; --j) {
+      if (i == j) xi *= R(invd[j]);
+      const R xj = __shfl_sync(FULLMASK, xi, j - i0);
+      if (i < j) xi -= a[i * ld + j] * xj;
+    }
+    if (i < i1) x[i] = xi;
+    __syncwarp();
+    for (int r = lane; r < i0; r += 32) {
+      R sacc = R(0);
+      for (int j = i0; j < i1; ++j) sacc += a[r * ld + j] * x[j];
+      x[r] -= sacc;
+    }
+    __syncwarp();
+  }
+}
+
+// Solve M x = b for the FP64 right-hand side b; x written as double.
+// FP64: plain LU solve. Otherwise: FP32 solve, then `ir` sweeps of
+// r = b - M0 x (accumulated in FP64 against the assembled matrix M0), x += M^-1 r.
+template <int NW, int PREC>
+__device__ void solve(Cta<NW>& c, int n, const double* b, double* x, int ir) {
+  constexpr int NT = NW * 32;
+  using P = Policy<PREC>;
+  if constexpr (!P::IR) {
+    for (int i = c.tid; i < n; i += NT) x[i] = b[c.perm[i]];
+    __syncthreads();
+    if (c.warp == 0) lu_solve_warp<double>(reinterpret_cast<double*>(c.M), n, c.invd, x, c.lane);
+    __syncthreads();
+  } else {
+    const float* a = reinterpret_cast<const float*>(c.M);
+    const typename P::ASM* M0 = reinterpret_cast<const typename P::ASM*>(c.M0);
+    float* xf = reinterpret_cast<float*>(c.sc);  // scratch vector reused as float
+    for (int i = c.tid; i < n; i += NT) xf[i] = (float)b[c.perm[i]];
+    __syncthreads();
+    if (c.warp == 0) lu_solve_warp<float>(a, n, c.invd, xf, c.lane);
+    __syncthreads();
+    for (int i = c.tid; i < n; i += NT) x[i] = (double)xf[i];
+    __syncthreads();
+    const int ld = odd_ld(n);
+    for (int sweep = 0; sweep < ir; ++sweep) {
+      for (int i = c.warp; i < n; i += NW) {
+        double acc = 0.0;
+        for (int j = c.lane; j < n; j += 32) acc += (double)M0[i * ld + j] * x[j];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(FULLMASK, acc, o);
+        if (c.lane == 0) c.rr[i] = b[i] - acc;
+      }
+      __syncthreads();
+      for (int i = c.tid; i < n; i += NT) xf[i] = (float)c.rr[c.perm[i]];
+      __syncthreads();
+      if (c.warp == 0) lu_solve_warp<float>(a, n, c.invd, xf, c.lane);
+      __syncthreads();
+      for (int i = c.tid; i < n; i += NT) x[i] += (double)xf[i];
+      __syncthreads();
+    }
+  }
+}
+
+// Assemble the iteration matrix (fac > 0) or the Jacobian (fac == 0, jac_only) in
+// the policy's assembly precision, then give the LU its own copy when they differ.
+template <int NW, int PREC>
+__device__ void build_matrix(const DevMech& m, Cta<NW>& c, const Scal& s, const double* y, const double* f,
+                             double fac, bool jac_only) {
+  using P = Policy<PREC>;
+  if constexpr (!P::IR) {
+    assemble<NW, double>(m, c, s, y, f, fac, jac_only, c.M);
+  } else {
+    assemble<NW, typename P::ASM>(m, c, s, y, f, fac, jac_only, c.M0);
+    if (jac_only) return;
+    const int n = m.K + 1, ld = odd_ld(n);
+    const typename P::ASM* src = reinterpret_cast<const typename P::ASM*>(c.M0);
+    float* dst = reinterpret_cast<float*>(c.M);
+    for (int i = c.warp; i < n; i += NW)
+      for (int j = c.lane; j < n; j += 32) dst[i * ld + j] = (float)src[i * ld + j];
+    __syncthreads();
+  }
+}
+
+// WRMS norm of e with scale atol + rtol max(|ya|, |yb|).
+template <int NW>
+__device__ double wrms(Cta<NW>& c, int n, const double* e, const double* ya, const double* yb,
+                       double rtol, double atol) {
+  constexpr int NT = NW * 32;
+  double part[1] = {0.0};
+  for (int i = c.tid; i < n; i += NT) {
+    const double sc = atol + rtol * fmax(fabs(ya[i]), fabs(yb[i]));
+    const double r = e[i] / sc;
+    part[0] += r * r;
+  }
+  c.sum(part);
+  return sqrt(part[0] / n);
+}
+
+// Hairer-Wanner starting step (Solving ODEs I, Sec. II.4) in the WRMS norm with
+// scale atol + rtol |y0|, exponent 1/4, clamped to dt; a vanishing derivative
+// selects the whole interval. Uses f0 = f(y0) (already in c.f0) and c.ys, c.fv.
+template <int NW>
+__device__ double starting_step(const DevMech& m, Cta<NW>& c, double p, double dt, double rtol,
+                                double atol) {
+  constexpr int NT = NW * 32;
+  const int n = m.K + 1;
+  const double d0 = wrms(c, n, c.y, c.y, c.y, rtol, atol);
+  const double d1 = wrms(c, n, c.f0, c.y, c.y, rtol, atol);
+  double ha = (d1 > 1e-300) ? 0.01 * d0 / d1 : dt;
+  ha = fmin(ha, dt);
+  for (int i = c.tid; i < n; i += NT) c.ys[i] = c.y[i] + ha * c.f0[i];
+  __syncthreads();
+  eval_rhs<NW, false>(m, c, c.ys, p, c.fv);
+  for (int i = c.tid; i < n; i += NT) c.rr[i] = c.fv[i] - c.f0[i];
+  __syncthreads();
+  const double d2 = wrms(c, n, c.rr, c.y, c.y, rtol, atol) / ha;
+  const double mx = fmax(d1, d2);
+  const double hb = (mx > 1e-300) ? pow(0.01 / mx, 0.25) : dt;
+  return fmin(fmin(100.0 * ha, hb), dt);
+}
+
+// Mass enthalpy and heat capacity at T for mass fractions Y (CTA sums).
+template <int NW>
+__device__ void h_cp_mass(const DevMech& m, Cta<NW>& c, double T, const double* Y, double& h,
+                          double& cp) {
+  constexpr int NT = NW * 32;
+  const double invT = 1.0 / T;
+  double part[2] = {0.0, 0.0};
+  for (int k = c.tid; k < m.K; k += NT) {
+    const double* a = m.nasa + 36 * k;
+    a += (T < a[34]) ? 0 : 17;
+    const double cpr = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
+    const double hr = a[5] + T * (a[6] + T * (a[7] + T * (a[8] + T * a[9]))) + a[10] * invT;
+    part[0] += Y[k] * hr * m.invW[k];
+    part[1] += Y[k] * cpr * m.invW[k];
+  }
+  c.sum(part);
+  h = part[0] * kRc * T;
+  cp = part[1] * kRc;
+}
+
+// ---------------------------------------------------------------------------
+// one cell
+// ---------------------------------------------------------------------------
+template <int NW, int PREC>
+__device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs& args, Cta<NW>& c) {
+  using R = typename Policy<PREC>::LU;
+  constexpr int NT = NW * 32;
+  const DevMech& m = job.m;
+  const int K = m.K, n = K + 1;
+  const double p = job.p[cell];
+  const double dt = args.dt, rtol = args.rtol, atol = args.atol;
+  // load (coalesced over species)
+  if (c.tid == 0) c.y[0] = job.T[cell];
+  for (int k = c.tid; k < K; k += NT) c.y[1 + k] = job.Y[(size_t)cell * K + k];
+  __syncthreads();
+  int status = CHEM_CELL_OK;
+  {
+    double part[1] = {0.0};
+    for (int i = c.tid; i < n; i += NT) part[0] += isfinite(c.y[i]) ? 0.0 : 1.0;
+    c.sum(part);
+    if (part[0] > 0.0 || !(c.y[0] > 0.0) || !(p > 0.0)) status = CHEM_CELL_NONFINITE;
+  }
+  int steps = 0, rejects = 0;
+  double h_first = 0.0;
+  if (status == CHEM_CELL_OK) {
+    double h_target, cp_dummy;
+    h_cp_mass(m, c, c.y[0], c.y + 1, h_target, cp_dummy);
+    // initial step
+    double h = -1.0;
+    if (args.use_h0 && job.h0) {
+      const double g = job.h0[cell];
+      if (isfinite(g) && g > 0.0) h = fmin(g, dt);
+    }
+    if (h <= 0.0) {
+      eval_rhs<NW, false>(m, c, c.y, p, c.f0);
+      h = starting_step(m, c, p, dt, rtol, atol);
+    }
+    double t = 0.0;
+    bool after_reject = false;
+    R* Mm = reinterpret_cast<R*>(c.M);
+    while (true) {
+      if (dt - t <= 1e-12 * dt) break;
+      if (steps >= args.max_steps) { status = CHEM_CELL_MAX_STEPS; break; }
+      if (!(h >= kHmin)) { status = CHEM_CELL_H_UNDERFLOW; break; }  // also catches NaN
+      if (t + h > dt) h = dt - t;
+      ++steps;
+      // Jacobian and f0 at y; iteration matrix; LU
+      const Scal s = eval_rhs<NW, true>(m, c, c.y, p, c.f0);
+      build_matrix<NW, PREC>(m, c, s, c.y, c.f0, 1.0 / (h * kRodasGamma), false);
+      const int info = lu_factor<NW, R>(c, Mm, n);
+      double err;
+      if (info != 0) {
+        err = NAN;
+      } else {
+        const double invh = 1.0 / h;
+#pragma unroll 1
+        for (int st = 0; st < 6; ++st) {
+          const double* fs = c.f0;
+          if (st > 0) {
+            for (int i = c.tid; i < n; i += NT) {
+              double v = c.y[i];
+              for (int j = 0; j < st; ++j) v += c_rodasA[st][j] * c.u[j * n + i];
+              c.ys[i] = v;
+            }
+            __syncthreads();
+            eval_rhs<NW, false>(m, c, c.ys, p, c.fv);
+            fs = c.fv;
+          }
+          for (int i = c.tid; i < n; i += NT) {
+            double v = fs[i];
+            for (int j = 0; j < st; ++j) v += c_rodasC[st][j] * invh * c.u[j * n + i];
+            c.rr[i] = v;
+          }
+          __syncthreads();
+          // rr is also the IR residual buffer: copy the stage RHS to fv first
+          for (int i = c.tid; i < n; i += NT) c.fv[i] = c.rr[i];
+          __syncthreads();
+          solve<NW, PREC>(c, n, c.fv, c.u + st * n, args.ir_sweeps);
+        }
+        for (int i = c.tid; i < n; i += NT) {
+          double v = c.y[i];
+#pragma unroll
+          for (int j = 0; j < 6; ++j) v += c_rodasM[j] * c.u[j * n + i];
+          c.yn[i] = v;
+        }
+        __syncthreads();
+        err = wrms(c, n, c.u + 5 * n, c.y, c.yn, rtol, atol);
+      }
+      if (!(err <= 1.0)) {
+        ++rejects;
+        after_reject = true;
+        const double fac = isfinite(err) ? fmax(kSafety * pow(err, -0.25), kFacMin) : kFacMin;
+        h *= fac;
+        continue;
+      }
+      t += h;
+      for (int i = c.tid; i < n; i += NT) c.y[i] = c.yn[i];
+      __syncthreads();
+      if (h_first == 0.0) h_first = h;
+      double fac = err > 0.0 ? kSafety * pow(err, -0.25) : kFacMax;
+      fac = fmin(fmax(fac, kFacMin), after_reject ? 1.0 : kFacMax);
+      after_reject = false;
+      h *= fac;
+    }
+    // temperature from the conserved mass enthalpy (Newton, |dT| < 1e-10 T)
+    if (status == CHEM_CELL_OK) {
+      double T = c.y[0];
+      for (int it = 0; it < 50; ++it) {
+        double hm, cpm;
+        h_cp_mass(m, c, T, c.y + 1, hm, cpm);
+        const double dT = (hm - h_target) / cpm;
+        T -= dT;
+        if (fabs(dT) < 1e-10 * T) break;
+      }
+      if (!(T >= kTmin && T <= kTmax)) status = CHEM_CELL_T_RANGE;
+      else if (c.tid == 0) c.y[0] = T;
+      __syncthreads();
+    }
+  }
+  // store (the last accepted state for failed cells)
+  if (status != CHEM_CELL_NONFINITE) {
+    if (c.tid == 0) job.T[cell] = c.y[0];
+    for (int k = c.tid; k < K; k += NT) job.Y[(size_t)cell * K + k] = c.y[1 + k];
+  }
+  if (c.tid == 0) {
+    if (job.st.substeps) job.st.substeps[cell] = steps;
+    if (job.st.rejects) job.st.rejects[cell] = rejects;
+    if (job.st.h_first) job.st.h_first[cell] = h_first;
+    if (job.st.status) job.st.status[cell] = status;
+    if (job.cost_out) job.cost_out[cell] = (float)steps;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+template <int NW, int PREC>
+__global__ void __launch_bounds__(NW * 32) k_integrate(const __grid_constant__ IntegrateArgs args) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ long long s_work;
+  const Layout L = make_layout(args.smem_K, args.smem_I, PREC);
+  Cta<NW> c;
+  c.bind(smem, L);
+  for (long long it = 0;; ++it) {
+    long long w;
+    if (args.sched == SCHED_PLAIN) {
+      if (it > 0) break;
+      w = blockIdx.x;
+    } else if (args.sched == SCHED_STATIC) {
+      w = blockIdx.x + it * (long long)gridDim.x;
+    } else {
+      if (threadIdx.x == 0) s_work = atomicAdd(args.queue, 1);
+      __syncthreads();
+      w = s_work;
+      __syncthreads();
+    }
+    if (w >= args.n_total) break;
+    const long long g = args.perm ? args.perm[w] : w;
+    int j = 0;
+    while (j + 1 < args.n_jobs && g >= args.jobs[j + 1].offset) ++j;
+    integrate_cell<NW, PREC>(args.jobs[j], g - args.jobs[j].offset, args, c);
+  }
+}
+
+struct DiagArgs {
+  DevMech m;
+  int64_t n;
+  const double *T, *p, *Y;
+  double* out;
+  double dt, rtol, atol;
+  int what;  // 0 rhs, 1 jacobian, 2 h0
+};
+
+template <int NW, int PREC>
+__global__ void __launch_bounds__(NW * 32) k_diag(const __grid_constant__ DiagArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  using A = typename Policy<PREC>::ASM;
+  const Layout L = make_layout(a.m.K, a.m.I, PREC);
+  Cta<NW> c;
+  c.bind(smem, L);
+  constexpr int NT = NW * 32;
+  const int K = a.m.K, n = K + 1, ld = odd_ld(n);
+  for (int64_t cell = blockIdx.x; cell < a.n; cell += gridDim.x) {
+    if (c.tid == 0) c.y[0] = a.T[cell];
+    for (int k = c.tid; k < K; k += NT) c.y[1 + k] = a.Y[(size_t)cell * K + k];
+    __syncthreads();
+    const double p = a.p[cell];
+    if (a.what == 0) {
+      eval_rhs<NW, false>(a.m, c, c.y, p, c.f0);
+      for (int i = c.tid; i < n; i += NT) a.out[(size_t)cell * n + i] = c.f0[i];
+    } else if (a.what == 1) {
+      const Scal s = eval_rhs<NW, true>(a.m, c, c.y, p, c.f0);
+      build_matrix<NW, PREC>(a.m, c, s, c.y, c.f0, 0.0, true);
+      const A* J = reinterpret_cast<const A*>(Policy<PREC>::IR ? c.M0 : c.M);
+      for (int i = c.warp; i < n; i += NW)
+        for (int j = c.lane; j < n; j += 32) a.out[(size_t)cell * n * n + i * n + j] = (double)J[i * ld + j];
+    } else {
+      eval_rhs<NW, false>(a.m, c, c.y, p, c.f0);
+      const double h = starting_step(a.m, c, p, a.dt, a.rtol, a.atol);
+      if (c.tid == 0) a.out[cell] = h;
+    }
+    __syncthreads();
+  }
+}
+
+struct LuArgs {
+  int64_t n_mat;
+  int dim;
+  const double *A, *b;
+  double* x;
+  int* info;
+  int ir;
+};
+
+template <int NW, int PREC>
+__global__ void __launch_bounds__(NW * 32) k_lu_solve(const __grid_constant__ LuArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  using P = Policy<PREC>;
+  using R = typename P::LU;
+  const Layout L = make_layout(a.dim - 1, 1, PREC);
+  Cta<NW> c;
+  c.bind(smem, L);
+  constexpr int NT = NW * 32;
+  const int n = a.dim, ld = odd_ld(n);
+  R* M = reinterpret_cast<R*>(c.M);
+  for (int64_t s = blockIdx.x; s < a.n_mat; s += gridDim.x) {
+    const double* As = a.A + (size_t)s * n * n;
+    for (int i = c.warp; i < n; i += NW)
+      for (int j = c.lane; j < n; j += 32) {
+        const typename P::ASM v = (typename P::ASM)As[i * n + j];
+        M[i * ld + j] = (R)v;
+        if constexpr (P::IR) reinterpret_cast<typename P::ASM*>(c.M0)[i * ld + j] = v;
+      }
+    for (int i = c.tid; i < n; i += NT) c.fv[i] = a.b[(size_t)s * n + i];
+    __syncthreads();
+    const int info = lu_factor<NW, R>(c, M, n);
+    if (info == 0) solve<NW, PREC>(c, n, c.fv, c.u, a.ir);
+    for (int i = c.tid; i < n; i += NT) a.x[(size_t)s * n + i] = info == 0 ? c.u[i] : NAN;
+    if (c.tid == 0 && a.info) a.info[s] = info;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+template <class KernelT>
+static cudaError_t prep(KernelT k, size_t smem) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int NW, int PREC>
+static cudaError_t launch_integrate_t(const IntegrateArgs& a, int grid, cudaStream_t st) {
+  const size_t smem = smem_bytes(a.smem_K, a.smem_I, PREC);
+  cudaError_t e = prep(k_integrate<NW, PREC>, smem);
+  if (e != cudaSuccess) return e;
+  k_integrate<NW, PREC><<<grid, NW * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_integrate(const IntegrateArgs& a, int block, int prec, int grid, cudaStream_t st) {
+#define LI(P)                                                                       \
+  do {                                                                              \
+    if (block == 64) return launch_integrate_t<2, P>(a, grid, st);                  \
+    if (block == 256) return launch_integrate_t<8, P>(a, grid, st);                 \
+    return launch_integrate_t<4, P>(a, grid, st);                                   \
+  } while (0)
+  if (prec == PREC_FP64) LI(PREC_FP64);
+  if (prec == PREC_MIXED) LI(PREC_MIXED);
+  LI(PREC_FP32ASM);
+#undef LI
+}
+
+cudaError_t occupancy_integrate(int block, int prec, int K, int I, int* ctas_per_sm) {
+  const size_t smem = smem_bytes(K, I, prec);
+  cudaError_t e;
+#define OCC(NW, P)                                                                         \
+  do {                                                                                     \
+    e = prep(k_integrate<NW, P>, smem);                                                    \
+    if (e != cudaSuccess) return e;                                                        \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_integrate<NW, P>, \
+                                                         NW * 32, smem);                   \
+  } while (0)
+#define OCCP(P)                  \
+  do {                           \
+    if (block == 64) OCC(2, P);  \
+    if (block == 256) OCC(8, P); \
+    OCC(4, P);                   \
+  } while (0)
+  if (prec == PREC_FP64) OCCP(PREC_FP64);
+  if (prec == PREC_MIXED) OCCP(PREC_MIXED);
+  OCCP(PREC_FP32ASM);
+#undef OCCP
+#undef OCC
+}
+
+template <int PREC, class ArgT, class KernelT>
+static cudaError_t launch_simple(KernelT k, const ArgT& a, size_t smem, int grid, cudaStream_t st) {
+  cudaError_t e = prep(k, smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, 128, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag(const DevMech& m, int64_t n, const double* T, const double* p, const double* Y,
+                        double* out, double dt, double rtol, double atol, int what, int prec,
+                        cudaStream_t st) {
+  DiagArgs a;
+  a.m = m;
+  a.n = n;
+  a.T = T;
+  a.p = p;
+  a.Y = Y;
+  a.out = out;
+  a.dt = dt;
+  a.rtol = rtol;
+  a.atol = atol;
+  a.what = what;
+  const size_t smem = smem_bytes(m.K, m.I, prec);
+  const int grid = (int)(n < 65535 ? n : 65535);
+  if (prec == PREC_FP64) return launch_simple<PREC_FP64>(k_diag<4, PREC_FP64>, a, smem, grid, st);
+  if (prec == PREC_MIXED) return launch_simple<PREC_MIXED>(k_diag<4, PREC_MIXED>, a, smem, grid, st);
+  return launch_simple<PREC_FP32ASM>(k_diag<4, PREC_FP32ASM>, a, smem, grid, st);
+}
+
+cudaError_t launch_lu_solve(int64_t n_mat, int dim, const double* A, const double* b, double* x,
+                            int* info, int prec, int ir, cudaStream_t st) {
+  LuArgs a;
+  a.n_mat = n_mat;
+  a.dim = dim;
+  a.A = A;
+  a.b = b;
+  a.x = x;
+  a.info = info;
+  a.ir = ir;
+  const size_t smem = smem_bytes(dim - 1, 1, prec);
+  const int grid = (int)(n_mat < 65535 ? n_mat : 65535);
+  if (prec == PREC_FP64) return launch_simple<PREC_FP64>(k_lu_solve<4, PREC_FP64>, a, smem, grid, st);
+  if (prec == PREC_MIXED) return launch_simple<PREC_MIXED>(k_lu_solve<4, PREC_MIXED>, a, smem, grid, st);
+  return launch_simple<PREC_FP32ASM>(k_lu_solve<4, PREC_FP32ASM>, a, smem, grid, st);
+}
+
+}  // namespace chem

@@ -1,0 +1,325 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI.
+
+Bound for integrated states (rtol 1e-8, atol 1e-12): |dT| <= 1e-6 T and
+|dY_k| <= 1e-8 + 1e-5 |Y_k|, for the FP64 and the mixed-precision forms.
+"""
+import numpy as np
+import pytest
+
+import mechs
+from paper_2112_05834_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL, ATOL = 1e-8, 1e-12
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_05834_gb300 import _build
+
+    _build.build()
+    import paper_2112_05834_gb300 as p
+
+    p.load()
+    return p
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+
+    oracle.build()
+    return oracle
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), device="cuda", dtype=torch.float64)
+
+
+def _assert_bound(T, Y, ref, what=""):
+    dT = np.abs(T - ref["T"]) / ref["T"]
+    dY = np.abs(Y - ref["Y"]) / (1e-8 + 1e-5 * np.abs(ref["Y"]))
+    assert dT.max() <= 1e-6, f"{what}: max |dT|/T = {dT.max():.3e} at cell {np.argmax(dT)}"
+    assert dY.max() <= 1.0, f"{what}: max |dY|/bound = {dY.max():.3e}"
+
+
+def _mech_cases():
+    return {
+        "h2_10": synth.mechanism_preset("h2_10"),
+        "c_54": synth.mechanism_preset("c_54"),
+        "falloff_mix": synth.gen_mechanism(5, ("C", "H", "O", "N"), 30, 120, n_third_body=10,
+                                           n_troe=8, n_lindemann=8, Ea_R_max=30000.0),
+        "branch": mechs.with_high_branch(synth.mechanism_preset("c_32")),
+    }
+
+
+def _states(m, n=24, seed=3, p=40e5):
+    st = synth.gen_states(m, n, seed=seed, p=p, classes=synth.MIXED_CLASSES)
+    # add states straddling T_mid = 1000 K
+    st.T[:4] = [999.9, 1000.0, 1000.1, 1300.0]
+    return st
+
+
+# ------------------------------------------------------------------ RHS / Jacobian / h0
+@pytest.mark.parametrize("name", list(_mech_cases().keys()))
+def test_rhs_parity(pkg, orc, name):
+    m = _mech_cases()[name]
+    st = _states(m)
+    integ = pkg.Integrator(m)
+    f = integ.eval_rhs(_dev(st.T), _dev(st.p), _dev(st.Y)).cpu().numpy()
+    M = orc.Mech(m)
+    nu = np.abs(m.net_stoich())
+    for c in range(st.T.shape[0]):
+        y = np.concatenate([[st.T[c]], st.Y[c]])
+        fr = orc.rhs(M, st.p[c], y)
+        _, _, q = orc.rates(M, st.p[c], y)
+        rho = st.p[c] / (8.31446261815324e7 * st.T[c] * np.sum(st.Y[c] / m.W))
+        gross = np.concatenate([[np.abs(fr[0])], m.W * (nu @ np.abs(q)) / rho])
+        gross[0] = max(gross[0], np.abs(fr[0]))
+        err = np.abs(f[c] - fr)
+        assert np.all(err <= 1e-11 * (np.abs(fr) + gross) + 1e-300), (name, c, np.max(err / (np.abs(fr) + gross + 1e-300)))
+
+
+@pytest.mark.parametrize("name", list(_mech_cases().keys()))
+def test_jacobian_parity(pkg, orc, name):
+    m = _mech_cases()[name]
+    st = _states(m, n=12)
+    M = orc.Mech(m)
+    for precision, tol in ((0, 1e-10), (1, 1e-10), (2, 2e-5)):
+        integ = pkg.Integrator(m, precision=precision)
+        J = integ.eval_jacobian(_dev(st.T), _dev(st.p), _dev(st.Y)).cpu().numpy()
+        for c in range(st.T.shape[0]):
+            y = np.concatenate([[st.T[c]], st.Y[c]])
+            Jr = orc.jac(M, st.p[c], y)
+            row = np.abs(Jr).max(axis=1, keepdims=True) + 1e-300
+            err = np.abs(J[c] - Jr) / (np.abs(Jr) + row)
+            assert err.max() <= tol, (name, precision, c, err.max())
+
+
+def test_starting_step_parity(pkg, orc):
+    m = synth.mechanism_preset("c_54")
+    st = _states(m, n=32)
+    integ = pkg.Integrator(m)
+    h = integ.eval_h0(_dev(st.T), _dev(st.p), _dev(st.Y), 1e-6, RTOL, ATOL).cpu().numpy()
+    M = orc.Mech(m)
+    for c in range(32):
+        y = np.concatenate([[st.T[c]], st.Y[c]])
+        np.testing.assert_allclose(h[c], orc.h0(M, st.p[c], y, 1e-6, RTOL, ATOL), rtol=1e-10)
+
+
+# ------------------------------------------------------------------ LU
+@pytest.mark.parametrize("dim,cond", [(3, 10.0), (55, 1e3), (101, 1e4), (128, 1e2)])
+def test_lu_solve_parity(pkg, orc, dim, cond):
+    rng = np.random.default_rng(dim)
+    n_mat = 37
+    A = np.empty((n_mat, dim, dim))
+    for s in range(n_mat):
+        U, _ = np.linalg.qr(rng.standard_normal((dim, dim)))
+        V, _ = np.linalg.qr(rng.standard_normal((dim, dim)))
+        A[s] = U @ np.diag(np.logspace(0, -np.log10(cond), dim)) @ V.T
+    b = rng.standard_normal((n_mat, dim))
+    ref = np.stack([orc.lu_solve(*orc.lu_factor(A[s])[:2], b[s]) for s in range(n_mat)])
+    # the FP32-assembly form refines towards the FP32-rounded matrix
+    A32 = A.astype(np.float32).astype(np.float64)
+    ref32 = np.stack([orc.lu_solve(*orc.lu_factor(A32[s])[:2], b[s]) for s in range(n_mat)])
+    for precision, ir, tol, r in ((0, 0, 1e-13, ref), (1, 3, 1e-12, ref), (1, 0, 1e-5, ref),
+                                  (2, 3, 1e-12, ref32)):
+        x, info = pkg.lu_solve_batched(_dev(A), _dev(b), precision=precision, ir_sweeps=ir)
+        x = x.cpu().numpy()
+        assert np.all(info.cpu().numpy() == 0)
+        err = np.abs(x - r).max(axis=1) / np.abs(r).max(axis=1)
+        assert err.max() <= tol * cond, (precision, ir, err.max())
+
+
+def test_lu_singular(pkg):
+    A = np.zeros((2, 4, 4))
+    A[0] = np.eye(4)
+    A[1] = np.eye(4)
+    A[1, 2, 2] = 0.0
+    b = np.ones((2, 4))
+    x, info = pkg.lu_solve_batched(_dev(A), _dev(b))
+    assert list(info.cpu().numpy()) == [0, 3]
+    assert np.all(np.isnan(x.cpu().numpy()[1]))
+
+
+# ------------------------------------------------------------------ integration
+def _run(pkg, m, st, dt, **opt):
+    integ = pkg.Integrator(m, **opt)
+    T, p, Y = _dev(st.T), _dev(st.p), _dev(st.Y)
+    integ.integrate(T, p, Y, dt, RTOL, ATOL)
+    s = integ.stats(st.T.shape[0])
+    torch.cuda.synchronize()
+    out = {"T": T.cpu().numpy(), "Y": Y.cpu().numpy()}
+    out.update({k: v.cpu().numpy() for k, v in s.items()})
+    integ.close()
+    return out
+
+
+_REF_CACHE = {}
+
+
+def _oracle_ref(orc, name, n, seed=1):
+    key = (name, n, seed)
+    if key not in _REF_CACHE:
+        m, st, dt = synth.workload(name, n_cells=n, state_seed=seed)
+        _REF_CACHE[key] = (m, st, dt, orc.integrate(m, st.T, st.p, st.Y, dt, RTOL, ATOL))
+    return _REF_CACHE[key]
+
+
+@pytest.mark.parametrize("name,n", [("h2_10_1k", 1000), ("c54_65k", 333), ("c100_262k", 161)])
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_integrate_parity(pkg, orc, name, n, precision):
+    m, st, dt, ref = _oracle_ref(orc, name, n)
+    assert np.all(ref["status"] == 0)
+    g = _run(pkg, m, st, dt, precision=precision)
+    assert np.all(g["status"] == 0)
+    _assert_bound(g["T"], g["Y"], ref, f"{name} precision={precision}")
+    ratio = g["substeps"].sum() / ref["substeps"].sum()
+    print(f"{name} precision={precision}: substeps gpu/oracle = {ratio:.4f}, "
+          f"rejects gpu {g['rejects'].sum()} oracle {ref['rejects'].sum()}")
+    if precision in (0, 1):
+        # the same method up to rounding: step counts agree closely
+        assert abs(ratio - 1.0) <= 0.05, ratio
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_conservation_on_gpu(pkg, orc, precision):
+    m, st, dt, ref = _oracle_ref(orc, "c54_65k", 333)
+    g = _run(pkg, m, st, dt, precision=precision)
+    print("precision", precision, "max |sum Y - 1| =", np.abs(g["Y"].sum(axis=1) - 1.0).max())
+    steps = g["substeps"]
+    assert np.all(np.abs(g["Y"].sum(axis=1) - 1.0) <= 1e-13 * (1 + steps))
+    el0 = (st.Y / m.W) @ m.elem
+    el1 = (g["Y"] / m.W) @ m.elem
+    assert np.all(np.abs(el1 - el0) <= 1e-13 * (1 + steps[:, None]) * np.abs(el0).max())
+
+
+def test_schedulers_bitwise_identical(pkg, orc):
+    """Per-cell results do not depend on how cells are scheduled (plain launch,
+    static persistent, queue) or on repetition."""
+    m, st, dt, ref = _oracle_ref(orc, "c54_65k", 333)
+    outs = [_run(pkg, m, st, dt, scheduler=s) for s in (0, 1, 2, 2)]
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o["T"], outs[0]["T"])
+        np.testing.assert_array_equal(o["Y"], outs[0]["Y"])
+        np.testing.assert_array_equal(o["substeps"], outs[0]["substeps"])
+
+
+@pytest.mark.parametrize("block", [64, 256])
+def test_block_sizes(pkg, orc, block):
+    m, st, dt, ref = _oracle_ref(orc, "c54_65k", 333)
+    g = _run(pkg, m, st, dt, block=block, precision=1)
+    _assert_bound(g["T"], g["Y"], ref, f"block={block}")
+
+
+def test_graph_replay(pkg, orc):
+    m, st, dt, ref = _oracle_ref(orc, "h2_10_1k", 1000)
+    integ = pkg.Integrator(m, graph=1)
+    p = _dev(st.p)
+    res = []
+    for _ in range(3):
+        T, Y = _dev(st.T), _dev(st.Y)
+        integ.integrate(T, p, Y, dt, RTOL, ATOL)
+        torch.cuda.synchronize()
+        res.append((T.cpu().numpy(), Y.cpu().numpy()))
+    for T, Y in res:
+        _assert_bound(T, Y, ref, "graph")
+    np.testing.assert_array_equal(res[0][0], res[2][0])
+
+
+def test_host_entry_point(pkg, orc):
+    m, st, dt, ref = _oracle_ref(orc, "h2_10_1k", 1000)
+    integ = pkg.Integrator(m)
+    T, Y = st.T.copy(), st.Y.copy()
+    integ.integrate_host(T, st.p.copy(), Y, dt, RTOL, ATOL)
+    g = _run(pkg, m, st, dt)
+    np.testing.assert_array_equal(T, g["T"])
+    np.testing.assert_array_equal(Y, g["Y"])
+
+
+def test_multi_mechanism_single_launch(pkg, orc):
+    """Four mechanisms (10, 32, 54, 100 species) in one launch give the same
+    per-cell results as four separate calls, and match the oracle."""
+    names = [("h2_10", 1e-5, synth.ATM), ("c_32", 1e-6, 60e5), ("c_54", 1e-6, 60e5), ("c_100", 1e-6, 40e5)]
+    jobs, singles, host = [], [], []
+    dt = 1e-6
+    for i, (nm, _, p) in enumerate(names):
+        m = synth.mechanism_preset(nm)
+        st = synth.gen_states(m, 97 + i, seed=10 + i, p=p, classes=synth.MIXED_CLASSES)
+        integ = pkg.Integrator(m)
+        jobs.append((integ, _dev(st.T), _dev(st.p), _dev(st.Y)))
+        singles.append(_run(pkg, m, st, dt))
+        host.append((m, st))
+    pkg.integrate_jobs(jobs, dt, RTOL, ATOL)
+    torch.cuda.synchronize()
+    for (integ, T, p, Y), s, (m, st) in zip(jobs, singles, host):
+        np.testing.assert_array_equal(T.cpu().numpy(), s["T"])
+        np.testing.assert_array_equal(Y.cpu().numpy(), s["Y"])
+        sub = slice(0, 24)
+        ref = orc.integrate(m, st.T[sub], st.p[sub], st.Y[sub], dt, RTOL, ATOL)
+        _assert_bound(s["T"][sub], s["Y"][sub], ref, m.species[0])
+
+
+# ------------------------------------------------------------------ edge cases
+def test_edge_cases(pkg):
+    m = synth.mechanism_preset("h2_10")
+    st = synth.gen_states(m, 8, seed=4, classes=synth.MIXED_CLASSES)
+    integ = pkg.Integrator(m)
+    # zero cells: no-op
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    integ.integrate(e, e, torch.empty((0, m.n_species), dtype=torch.float64, device="cuda"), 1e-6)
+    # invalid arguments
+    T, p, Y = _dev(st.T), _dev(st.p), _dev(st.Y)
+    with pytest.raises(pkg.ChemError):
+        integ.integrate(T, p, Y, -1.0)
+    with pytest.raises(pkg.ChemError):
+        integ.integrate(T, p, Y, 1e-6, rtol=0.0)
+    with pytest.raises(pkg.ChemError):
+        integ.set_option("block", 96)
+    # a non-finite cell is flagged and left alone; the others integrate
+    Tn = st.T.copy()
+    Tn[3] = np.nan
+    T = _dev(Tn)
+    integ.integrate(T, p, Y, 1e-6)
+    s = integ.stats(8)
+    status = s["status"].cpu().numpy()
+    assert status[3] == pkg.CELL_NONFINITE and np.all(np.delete(status, 3) == pkg.CELL_OK)
+    # step budget exhausted: MAX_STEPS, last accepted state kept (finite, normalised)
+    integ.set_option("max_steps", 2)
+    T, Y = _dev(st.T), _dev(st.Y)
+    integ.integrate(T, p, Y, 1e-3)
+    s = integ.stats(8)
+    assert np.any(s["status"].cpu().numpy() == pkg.CELL_MAX_STEPS)
+    assert np.all(np.isfinite(Y.cpu().numpy()))
+    assert integ.totals()["failed"] > 0
+    # final temperature outside [200, 6000] K
+    integ.set_option("max_steps", 100000)
+    Yn2 = np.zeros((1, m.n_species))
+    Yn2[0, m.roles["inert"]] = 1.0
+    T1 = _dev(np.array([6500.0]))
+    integ.integrate(T1, _dev(np.array([synth.ATM])), _dev(Yn2), 1e-6)
+    assert integ.stats(1)["status"].cpu().numpy()[0] == pkg.CELL_T_RANGE
+
+
+# ------------------------------------------------------------------ full size, sampled
+def test_full_size_sampled_parity(pkg, orc):
+    """The 54-species / 65,536-cell workload in the benchmark's launch
+    configuration (queue scheduler, mixed precision); sampled cells (per
+    temperature class and the costliest) against the oracle."""
+    m, st, dt = synth.workload("c54_65k")
+    g = _run(pkg, m, st, dt, precision=1, scheduler=2)
+    assert np.all(g["status"] == 0)
+    rng = np.random.default_rng(0)
+    pick = []
+    for k in range(3):
+        idx = np.flatnonzero(st.kind == k)
+        pick.extend(rng.choice(idx, 8, replace=False))
+    pick.extend(np.argsort(g["substeps"])[-8:])
+    pick = np.unique(np.array(pick))
+    ref = orc.integrate(m, st.T[pick], st.p[pick], st.Y[pick], dt, RTOL, ATOL)
+    _assert_bound(g["T"][pick], g["Y"][pick], ref, "c54 full size")
+    np.testing.assert_allclose(g["Y"].sum(axis=1), 1.0, atol=1e-10)
