@@ -40,6 +40,14 @@ SIGNATURES = {
     "chem_eval_h0": (C.c_int, [_P, _I64, _P, _P, _P, _D, _D, _D, _P, _P]),
     "chem_lu_solve_batched": (C.c_int, [_I64, _I32, _P, _P, _P, _P, _I32, _I32, _P]),
     "chem_rosenbrock_tableau": (None, [_P, _P, _P, _P, _P]),
+    "chem_mlp_create": (C.c_int, [_I32, C.c_uint64, _P]),
+    "chem_mlp_destroy": (C.c_int, [_P]),
+    "chem_mlp_train": (C.c_int, [_P, _I64, _P, _P, _P, _P, _P, _I32, _I32, _D, C.c_uint64, _P, _P]),
+    "chem_mlp_predict": (C.c_int, [_P, _I64, _P, _P, _P, _P, _P, _P]),
+    "chem_mlp_attach": (C.c_int, [_P, _P]),
+    "chem_mlp_get_params": (C.c_int, [_P, _P, _P]),
+    "chem_mlp_set_params": (C.c_int, [_P, _P, _I64]),
+    "chem_mlp_gradient": (C.c_int, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -254,3 +262,106 @@ def tableau():
                                    c.ctypes.data_as(C.c_void_p), m.ctypes.data_as(C.c_void_p),
                                    e.ctypes.data_as(C.c_void_p))
     return g.value, a, c, m, e
+
+
+class CostModel:
+    """Learned per-cell cost / initial-step model (wraps ``chem_mlp``; include/chem_mlp.h)."""
+
+    def __init__(self, n_species, seed=0):
+        h = C.c_void_p()
+        _check(load().chem_mlp_create(int(n_species), int(seed), C.byref(h)))
+        self.h = h
+        self.K = n_species
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().chem_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def train(self, T, p, Y, substeps, h_first, epochs=20, batch=8192, lr=1e-3, seed=0, stream=None):
+        """Adam on the logged (state, substeps, first step) samples; returns per-epoch losses."""
+        n = _check_cells(T, p, Y, self.K)
+        losses = np.zeros(max(epochs, 1), dtype=np.float32)
+        _check(load().chem_mlp_train(self.h, n, _dptr(T), _dptr(p), _dptr(Y), _dptr(substeps), _dptr(h_first),
+                                     int(epochs), int(batch), float(lr), int(seed),
+                                     losses.ctypes.data_as(C.c_void_p), _stream_ptr(stream)))
+        return losses[:epochs]
+
+    def predict(self, T, p, Y, stream=None):
+        """(ln substeps, ln first step) per cell as CUDA float32 tensors."""
+        import torch
+
+        n = _check_cells(T, p, Y, self.K)
+        lc = torch.empty(n, dtype=torch.float32, device=T.device)
+        lh = torch.empty(n, dtype=torch.float32, device=T.device)
+        _check(load().chem_mlp_predict(self.h, n, _dptr(T), _dptr(p), _dptr(Y), _dptr(lc), _dptr(lh),
+                                       _stream_ptr(stream)))
+        return lc, lh
+
+    def get_params(self):
+        nf = C.c_int64()
+        _check(load().chem_mlp_get_params(self.h, None, C.byref(nf)))
+        buf = np.zeros(nf.value, dtype=np.float32)
+        _check(load().chem_mlp_get_params(self.h, buf.ctypes.data_as(C.c_void_p), C.byref(nf)))
+        return buf
+
+    def set_params(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.float32)
+        _check(load().chem_mlp_set_params(self.h, buf.ctypes.data_as(C.c_void_p), buf.size))
+
+    def gradient(self, T, p, Y, substeps, h_first, stream=None):
+        """(loss, gradient over W1, b1, W2, b2, W3, b3) of one full-batch pass, no update."""
+        n = _check_cells(T, p, Y, self.K)
+        D = self.K + 2
+        nw = 128 * D + 128 + 128 * 128 + 128 + 2 * 128 + 2
+        g = np.zeros(nw, dtype=np.float32)
+        loss = C.c_float()
+        _check(load().chem_mlp_gradient(self.h, n, _dptr(T), _dptr(p), _dptr(Y), _dptr(substeps), _dptr(h_first),
+                                        C.byref(loss), g.ctypes.data_as(C.c_void_p), _stream_ptr(stream)))
+        return loss.value, g
+
+    def attach(self, integrator):
+        _check(load().chem_mlp_attach(integrator.h, self.h), integrator.h)
+        integrator._model = self
+
+
+def log_cells(integ, T, p, Y, dt, rtol=1e-8, atol=1e-12):
+    """Integrates copies of the given cells with the plain heuristic and index order,
+    returning the per-cell logs (substeps, h_first) the cost model trains on."""
+    order, h0 = integ.get_option("order"), integ.get_option("h0")
+    integ.set_option("order", 0)
+    integ.set_option("h0", 0)
+    T2, Y2 = T.clone(), Y.clone()
+    integ.integrate(T2, p, Y2, dt, rtol, atol)
+    s = integ.stats(T.shape[0])
+    integ.set_option("order", order)
+    integ.set_option("h0", h0)
+    return s["substeps"], s["h_first"]
+
+
+def train_cost_model(integ, mech, workload, n_cells, dt, seed=7, epochs=20, batch=8192, lr=1e-3):
+    """Trains a cost model on the logs of a separately seeded batch of the same
+    workload distribution and switches the integrator to the learned order and
+    initial step. Returns True."""
+    import torch
+
+    from . import synth
+
+    _, st, _ = synth.workload(workload, n_cells=n_cells, state_seed=1000 + seed)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    T = torch.tensor(st.T, device=dev)
+    p = torch.tensor(st.p, device=dev)
+    Y = torch.tensor(st.Y, device=dev)
+    sub, hf = log_cells(integ, T, p, Y, dt)
+    model = CostModel(mech.n_species, seed=seed)
+    model.train(T, p, Y, sub, hf, epochs=epochs, batch=batch, lr=lr, seed=seed)
+    model.attach(integ)
+    integ.set_option("order", 1)
+    integ.set_option("h0", 1)
+    return True

@@ -13,8 +13,9 @@
 chem_status chem_internal_mlp_predict(chem_handle h, const double* T, const double* p, const double* Y,
                                       int64_t n, cudaStream_t st, const float** cost, const double** h0);
 
-// Handle-owned float scratch of length n (reused between calls).
-chem_status chem_internal_scratch_float(chem_handle h, int64_t n, float** out);
+// Handle-owned per-cell buffers for the learned options (reused between calls):
+// predicted cost, predicted initial step, and a snapshot of the previous cost.
+chem_status chem_internal_learned_buffers(chem_handle h, int64_t n, float** cost, double** h0, float** snap);
 
 // Cell indices ordered by decreasing cost.
 chem_status chem_internal_cost_order(chem_handle h, const float* d_cost, int64_t n, cudaStream_t st,

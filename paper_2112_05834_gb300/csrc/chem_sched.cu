@@ -140,7 +140,7 @@ chem_status chem_internal_prepare_learned(chem_handle h, const chem_job* jobs, i
     float* snap = nullptr;
     if (h->order == 2) {
       // copy the previous cost aside, the running kernel writes the new one
-      chem_status s = chem_internal_scratch_float(h, n, &snap);
+      chem_status s = chem_internal_learned_buffers(h, n, nullptr, nullptr, &snap);
       if (s != CHEM_OK) return s;
       cudaMemcpyAsync(snap, cost, n * 4, cudaMemcpyDeviceToDevice, st);
       cost = snap;
@@ -312,7 +312,9 @@ chem_status chem_internal_autotune(chem_handle h, const IntegrateArgs& a, cudaSt
   return CHEM_OK;
 }
 
-chem_status chem_internal_scratch_float(chem_handle h, int64_t n, float** out) {
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+chem_status chem_internal_learned_buffers(chem_handle h, int64_t n, float** cost, double** h0, float** snap) {
   if (n > h->h0_cap) {
     cudaDeviceSynchronize();
     if (h->d_h0) {
@@ -321,11 +323,15 @@ chem_status chem_internal_scratch_float(chem_handle h, int64_t n, float** out) {
       cudaFree(h->d_h0);
       h->d_h0 = nullptr;
     }
-    // predicted cost (float) + predicted h0 (double) + snapshot (float)
-    chem_status s = chem_internal_alloc(h, &h->d_h0, (size_t)n * 16);
+    const size_t bytes = align256((size_t)n * 4) * 2 + align256((size_t)n * 8);
+    chem_status s = chem_internal_alloc(h, &h->d_h0, bytes);
     if (s != CHEM_OK) return s;
     h->h0_cap = n;
   }
-  *out = reinterpret_cast<float*>(static_cast<unsigned char*>(h->d_h0) + (size_t)h->h0_cap * 12);
+  unsigned char* b = static_cast<unsigned char*>(h->d_h0);
+  const size_t c4 = align256((size_t)h->h0_cap * 4), c8 = align256((size_t)h->h0_cap * 8);
+  if (cost) *cost = reinterpret_cast<float*>(b);
+  if (h0) *h0 = reinterpret_cast<double*>(b + c4);
+  if (snap) *snap = reinterpret_cast<float*>(b + c4 + c8);
   return CHEM_OK;
 }

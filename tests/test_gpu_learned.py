@@ -1,0 +1,134 @@
+"""Learned cost / initial-step model on the GPU: BF16 gradients against the FP64
+reference, training, and what the trained model gains over the method without it.
+The integrator's error control judges every step, so the learned form must meet
+the same parity bound against the oracle."""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import mlp_ref
+from paper_2112_05834_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL, ATOL = 1e-8, 1e-12
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_05834_gb300 import _build
+
+    _build.build()
+    import paper_2112_05834_gb300 as p
+
+    p.load()
+    return p
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), device="cuda", dtype=torch.float64)
+
+
+def _logged(pkg, name, n, seed):
+    m, st, dt = synth.workload(name, n_cells=n, state_seed=seed)
+    integ = pkg.Integrator(m)
+    T, p, Y = _dev(st.T), _dev(st.p), _dev(st.Y)
+    sub, hf = pkg.log_cells(integ, T, p, Y, dt)
+    return m, st, dt, integ, (T, p, Y, sub, hf)
+
+
+def test_gradient_matches_fp64_reference(pkg):
+    m, st, dt, integ, (T, p, Y, sub, hf) = _logged(pkg, "c54_65k", 2048, 41)
+    model = pkg.CostModel(m.n_species, seed=3)
+    model.train(T, p, Y, sub, hf, epochs=0)  # sets the normalisation only
+    params = model.get_params()
+    D = m.n_species + 2
+    norm, w = params[:2 * D + 4].astype(np.float64), params[2 * D + 4:].astype(np.float64)
+    loss_g, g_gpu = model.gradient(T, p, Y, sub, hf)
+    x = mlp_ref.features(st.T, st.p, st.Y)
+    xs = (x - norm[:D]) / norm[D:2 * D]
+    t = mlp_ref.targets(sub.cpu().numpy(), hf.cpu().numpy())
+    ts = (t - norm[2 * D:2 * D + 2]) / norm[2 * D + 2:]
+    L, g = mlp_ref.loss_and_grad(mlp_ref.unflatten(w, D), xs, ts)
+    assert abs(loss_g - L) <= 2e-2 * L, (loss_g, L)
+    gg = mlp_ref.unflatten(g_gpu.astype(np.float64), D)
+    for k in mlp_ref.ORDER:
+        rel = np.linalg.norm(gg[k] - g[k]) / np.linalg.norm(g[k])
+        print(k, "relative gradient error (BF16 vs FP64):", rel)
+        assert rel <= 3e-2, (k, rel)
+
+
+def test_training_learns_cost(pkg):
+    m, st, dt, integ, (T, p, Y, sub, hf) = _logged(pkg, "c54_65k", 16384, 42)
+    model = pkg.CostModel(m.n_species, seed=4)
+    losses = model.train(T, p, Y, sub, hf, epochs=20, batch=2048, lr=1e-3, seed=5)
+    print("loss per epoch:", losses)
+    assert losses[-1] < 0.5 * losses[0]
+    # held-out cells: predicted cost ranks the actual cost
+    m2, st2, dt2, integ2, (T2, p2, Y2, sub2, hf2) = _logged(pkg, "c54_65k", 4096, 43)
+    lc, lh = model.predict(T2, p2, Y2)
+    a = np.log(np.maximum(sub2.cpu().numpy(), 1))
+    b = lc.cpu().numpy()
+    ra, rb = np.argsort(np.argsort(a)), np.argsort(np.argsort(b))
+    rho = np.corrcoef(ra, rb)[0, 1]
+    print("Spearman(predicted, actual substeps) =", rho)
+    assert rho >= 0.8
+    err_h = np.abs(lh.cpu().numpy() - np.log(hf2.cpu().numpy()))
+    print("median |ln h0 error| =", np.median(err_h))
+
+
+def test_learned_form_gain_and_parity(pkg):
+    """Trained on one seeded batch, evaluated on another: the learned order and
+    initial step keep every cell within the parity bound and save work."""
+    import oracle
+
+    oracle.build()
+    m, st_tr, dt = synth.workload("c54_65k", n_cells=16384, state_seed=44)
+    _, st, _ = synth.workload("c54_65k", n_cells=8192, state_seed=45)
+    plain = pkg.Integrator(m, precision=1, scheduler=2)
+    learned = pkg.Integrator(m, precision=1, scheduler=2)
+    Ttr, ptr, Ytr = _dev(st_tr.T), _dev(st_tr.p), _dev(st_tr.Y)
+    sub, hf = pkg.log_cells(plain, Ttr, ptr, Ytr, dt)
+    model = pkg.CostModel(m.n_species, seed=6)
+    model.train(Ttr, ptr, Ytr, sub, hf, epochs=20, batch=4096, lr=1e-3, seed=7)
+    model.attach(learned)
+    learned.set_option("order", 1)
+    learned.set_option("h0", 1)
+    out = {}
+    for name, integ in (("plain", plain), ("learned", learned)):
+        T, p, Y = _dev(st.T), _dev(st.p), _dev(st.Y)
+        integ.integrate(T, p, Y, dt, RTOL, ATOL)  # warm-up
+        T, Y = _dev(st.T), _dev(st.Y)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        integ.integrate(T, p, Y, dt, RTOL, ATOL)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        s = integ.stats(st.T.shape[0])
+        out[name] = {"T": T.cpu().numpy(), "Y": Y.cpu().numpy(), "time": el,
+                     "substeps": s["substeps"].cpu().numpy(), "status": s["status"].cpu().numpy()}
+    for name, o in out.items():
+        print(name, "time %.4f s" % o["time"], "substeps", int(o["substeps"].sum()))
+        assert np.all(o["status"] == 0)
+    # parity of the learned form on sampled cells
+    rng = np.random.default_rng(1)
+    pick = np.unique(np.concatenate([rng.choice(8192, 24, replace=False),
+                                     np.argsort(out["learned"]["substeps"])[-8:]]))
+    ref = oracle.integrate(m, st.T[pick], st.p[pick], st.Y[pick], dt, RTOL, ATOL)
+    for name in ("plain", "learned"):
+        o = out[name]
+        assert np.all(np.abs(o["T"][pick] - ref["T"]) <= 1e-6 * ref["T"])
+        assert np.all(np.abs(o["Y"][pick] - ref["Y"]) <= 1e-8 + 1e-5 * np.abs(ref["Y"]))
+    # work: the learned initial step replaces the heuristic's 2 RHS evaluations per
+    # cell and must not cost extra steps overall
+    n = st.T.shape[0]
+    rhs_plain = 7 * out["plain"]["substeps"].sum() + 2 * n
+    rhs_learned = 7 * out["learned"]["substeps"].sum()
+    print("RHS evaluations plain", rhs_plain, "learned", rhs_learned,
+          "speed-up %.3f" % (out["plain"]["time"] / out["learned"]["time"]))
+    assert out["learned"]["substeps"].sum() <= 1.02 * out["plain"]["substeps"].sum()
+    assert rhs_learned < rhs_plain
