@@ -128,6 +128,40 @@ chem_status chem_integrate(chem_handle h, int64_t n_cells, double* T, const doub
 chem_status chem_integrate_host(chem_handle h, int64_t n_cells, double* T, const double* p,
                                 double* Y, double dt, double rtol, double atol, void* stream);
 
+/*
+ * Integration for callers that cannot allocate device memory. The paper has no
+ * counterpart: this exists for users of this library, not for the method.
+ *
+ * chem_integrate may grow handle-owned device buffers with cudaMalloc/cudaFree.
+ * Callers that cannot allow that -- code enqueueing work while a stream is being
+ * captured into a CUDA graph (allocation is not permitted during capture),
+ * applications whose device memory is fixed up front by their own pool, and
+ * callers that cannot accept the device synchronisation an allocation or free
+ * may imply -- use this entry point instead. It allocates nothing: the
+ * integration kernel's scratch (work-queue counter and per-cell statistics) lives
+ * in one fixed-size device array inside the library, sized for
+ * CHEM_NOALLOC_MAX_CELLS cells (about 1.3 MB), which every GPU that loads the
+ * library holds until the process exits.
+ *
+ * Arguments, layout and results are those of chem_integrate (device pointers,
+ * in-place T and Y, stream-ordered). The handle's precision, scheduler, block,
+ * ir_sweeps, max_steps and ctas_per_sm options apply; cells are taken in index
+ * order with the starting-step heuristic (the learned order and initial step,
+ * the autotuner and graph capture need handle-owned buffers and are not used).
+ * Per-cell statistics are not reported by this path.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. All calls share the one array and it keeps the last call's contents:
+ * the call clears what must start at zero (the queue counter) on `stream`, and
+ * calls that overlap on the GPU (concurrent streams or handles) race on it.
+ * Errors: CHEM_ERR_INVALID_ARG as for chem_integrate, and for
+ * n_cells > CHEM_NOALLOC_MAX_CELLS (split the batch); CHEM_ERR_CUDA.
+ */
+#define CHEM_NOALLOC_MAX_CELLS 65536
+chem_status chem_integrate_noalloc(chem_handle h, int64_t n_cells, double* T, const double* p, double* Y,
+                                   double dt, double rtol, double atol, void* stream);
+
 /* One batch of cells of one mechanism; pointers as in chem_integrate. */
 typedef struct {
   chem_handle h;

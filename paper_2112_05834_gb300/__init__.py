@@ -27,6 +27,7 @@ SIGNATURES = {
     "chem_destroy": (C.c_int, [_P]),
     "chem_integrate": (C.c_int, [_P, _I64, _P, _P, _P, _D, _D, _D, _P]),
     "chem_integrate_host": (C.c_int, [_P, _I64, _P, _P, _P, _D, _D, _D, _P]),
+    "chem_integrate_noalloc": (C.c_int, [_P, _I64, _P, _P, _P, _D, _D, _D, _P]),
     "chem_integrate_jobs": (C.c_int, [_P, _I32, _D, _D, _D, _P]),
     "chem_set_option": (C.c_int, [_P, C.c_char_p, _D]),
     "chem_get_option": (C.c_int, [_P, C.c_char_p, _P]),
