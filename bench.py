@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--forms", default="plain_fp64,headline")
+    ap.add_argument("--phases", action="store_true",
+                    help="one extra untimed step per form with per-phase cycle counters")
     return ap.parse_args()
 
 
@@ -167,7 +169,7 @@ def run_ours(args, rank, world):
 
     forms = {}
     plain = pkg.Integrator(m, precision=0, scheduler=0)
-    head = pkg.Integrator(m, precision=1, scheduler=2, ir_sweeps=2)
+    head = pkg.Integrator(m, precision=1, scheduler=2, ir_sweeps=1)
     learned = False
     if not args.no_learned and hasattr(pkg, "train_cost_model"):
         learned = pkg.train_cost_model(head, m, args.workload, n, dt, seed=7)
@@ -208,6 +210,14 @@ def run_ours(args, rank, world):
         tot = integ.totals()
         results[name] = {"ms_total": ms, "substeps": tot["substeps"], "failed": tot["failed"],
                          "rejects": tot["rejects"]}
+        if args.phases:
+            integ.set_option("profile", 1)
+            one(integ)
+            torch.cuda.synchronize()
+            ph = integ.phase_cycles()
+            integ.set_option("profile", 0)
+            tot_c = sum(ph.values())
+            results[name]["phases"] = {k: round(v / tot_c, 4) for k, v in ph.items()}
     # end to end through the host entry point (H2D of T, p, Y; D2H of T, Y inside the call)
     Th = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
     ph = torch.tensor(st.p).pin_memory().numpy()
@@ -266,7 +276,7 @@ def main():
     value = world * n * args.steps / (hd["ms_total"] / 1e3)
     ms_per_step = hd["ms_total"] / args.steps
     # roofline of the integration kernel (FP64 pipe): algorithmic FP64 flops / time
-    w_step = algorithmic_fp64_flops_per_step(m, 1, 2)
+    w_step = algorithmic_fp64_flops_per_step(m, 1, 1)
     substeps_per_launch = hd["substeps"]  # totals of the last launch
     achieved = w_step * substeps_per_launch / (ms_per_step / 1e3) / 1e12
     line = {
@@ -297,6 +307,10 @@ def main():
         line["plain_fp64"] = {"value": pv, "ms_per_step": pl["ms_total"] / args.steps,
                               "substeps_per_step": pl["substeps"],
                               "roofline_fp64_frac": a0 / FP64_PEAK_TFLOPS, "achieved_tflops": a0}
+        if "phases" in pl:
+            line["plain_fp64"]["phase_share"] = pl["phases"]
+    if "phases" in hd:
+        line["phase_share"] = hd["phases"]
         line["speedup_vs_plain_fp64"] = value / pv
     # integration kernel per step, plus (learned form) features, 2 GEMMs, head, 3 sort kernels
     line["gpu_launches"] = args.steps * (1 + (7 if learned else 0))

@@ -187,7 +187,7 @@ chem_status chem_integrate_jobs(const chem_job* jobs, int32_t n_jobs, double dt,
  *                 iteration matrix (state, rates, exp/log, error control in FP64);
  *                 2 = as 1 but with the Jacobian assembled in FP32 and the
  *                 refinement residual taken against that FP32 matrix
- *   "ir_sweeps"   0..3 refinement sweeps per solve in precision 1 and 2 (default 2)
+ *   "ir_sweeps"   0..3 refinement sweeps per solve in precision 1 and 2 (default 1)
  *   "scheduler"   0 = plain (one CTA per cell, hardware block order),
  *                 1 = static (persistent CTAs, fixed round-robin cells),
  *                 2 = queue (persistent CTAs pulling cells from a device counter)
@@ -201,6 +201,7 @@ chem_status chem_integrate_jobs(const chem_job* jobs, int32_t n_jobs, double dt,
  *                 while arguments repeat
  *   "autotune"    1 = time block sizes on a sample at the first call for a
  *                 new size and keep the fastest
+ *   "profile"     1 = accumulate per-phase cycle counters (chem_get_phase_cycles)
  * Errors: CHEM_ERR_INVALID_ARG for an unknown key or out-of-range value.
  */
 chem_status chem_set_option(chem_handle h, const char* key, double value);
@@ -219,6 +220,17 @@ chem_status chem_get_stats(chem_handle h, void* stream, int32_t* substeps, int32
 /* Totals of the last integration (host outputs, any may be NULL); synchronises. */
 chem_status chem_get_totals(chem_handle h, void* stream, int64_t* n_cells, int64_t* substeps,
                             int64_t* rejects, int64_t* failed);
+
+/*
+ * Per-phase SM cycles accumulated by integrations run with option "profile" = 1
+ * (host output cycles[8], summed over cells; thread 0 of each CTA reads the clock
+ * at the barriers that close each phase): 0 load + starting step, 1 RHS and
+ * Jacobian data at the step point, 2 iteration-matrix assembly, 3 factorisation,
+ * 4 stage RHS evaluations, 5 stage linear solves, 6 stage combination + error
+ * norm + control, 7 temperature recovery + store. reset != 0 zeroes the counters.
+ * Synchronises `stream`.
+ */
+chem_status chem_get_phase_cycles(chem_handle h, void* stream, uint64_t* cycles, int32_t reset);
 
 /* Last error message of the handle (or of the last chem_create when h is NULL). */
 const char* chem_last_error(chem_handle h);

@@ -41,6 +41,7 @@ SIGNATURES = {
     "chem_eval_h0": (C.c_int, [_P, _I64, _P, _P, _P, _D, _D, _D, _P, _P]),
     "chem_lu_solve_batched": (C.c_int, [_I64, _I32, _P, _P, _P, _P, _I32, _I32, _P]),
     "chem_rosenbrock_tableau": (None, [_P, _P, _P, _P, _P]),
+    "chem_get_phase_cycles": (C.c_int, [_P, _P, _P, _I32]),
     "chem_mlp_create": (C.c_int, [_I32, C.c_uint64, _P]),
     "chem_mlp_destroy": (C.c_int, [_P]),
     "chem_mlp_train": (C.c_int, [_P, _I64, _P, _P, _P, _P, _P, _I32, _I32, _D, C.c_uint64, _P, _P]),
@@ -201,6 +202,15 @@ class Integrator:
         _check(load().chem_get_totals(self.h, _stream_ptr(stream), *[C.byref(v) for v in vals]),
                self.h)
         return dict(zip(("n_cells", "substeps", "rejects", "failed"), (v.value for v in vals)))
+
+    PHASES = ("load+h0", "rhs+jac data", "assembly", "factorisation", "stage rhs", "stage solves",
+              "stage combine+control", "T recovery+store")
+
+    def phase_cycles(self, reset=True, stream=None):
+        """Per-phase SM cycles (option "profile" = 1) as a dict."""
+        buf = (C.c_uint64 * 8)()
+        _check(load().chem_get_phase_cycles(self.h, _stream_ptr(stream), buf, int(bool(reset))), self.h)
+        return dict(zip(self.PHASES, (int(v) for v in buf)))
 
     def eval_rhs(self, T, p, Y, stream=None):
         import torch

@@ -233,8 +233,9 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
     if (t >= 2) {
       ++n_fo;
       const double* tr4 = d->troe + 4 * o;
-      const double f8[8] = {std::log(d->A0[o]), d->b0[o], d->Ea0_R[o], tr4[0], tr4[1], tr4[2],
-                            tr4[3], 0.0};
+      // Troe: reciprocal T*** and T* (Lindemann rows leave them unused)
+      const double f8[8] = {std::log(d->A0[o]), d->b0[o], d->Ea0_R[o], tr4[0],
+                            t == 3 ? 1.0 / tr4[1] : 0.0, t == 3 ? 1.0 / tr4[2] : 0.0, tr4[3], 0.0};
       fo.insert(fo.end(), f8, f8 + 8);
     }
     // net stoichiometry per species
@@ -265,13 +266,24 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
     for (int k = 0; k < K; ++k) ptr[k + 1] = ptr[k] + (int)v[k].size();
     for (int k = 0; k < K; ++k) ent.insert(ent.end(), v[k].begin(), v[k].end());
   };
-  std::vector<int> sp_ptr, tr_ptr, jr_ptr(K + 1, 0);
+  std::vector<int> sp_ptr, tr_ptr;
   std::vector<int2> sp_ent, tr_ent;
-  std::vector<int4> jr_ent;
   flatten2(sp, sp_ptr, sp_ent);
   flatten2(tr, tr_ptr, tr_ent);
-  for (int k = 0; k < K; ++k) jr_ptr[k + 1] = jr_ptr[k] + (int)jr[k].size();
-  for (int k = 0; k < K; ++k) jr_ent.insert(jr_ent.end(), jr[k].begin(), jr[k].end());
+  // mass-action Jacobian contributions grouped by (row k, column j), fixed order
+  std::vector<int> pr_ptr(K + 1, 0), pr_col, pr_cptr(1, 0);
+  std::vector<int2> pr_ent;
+  for (int k = 0; k < K; ++k) {
+    std::vector<int4> ents = jr[k];  // (j, i, nu, slot)
+    std::stable_sort(ents.begin(), ents.end(), [](const int4& a, const int4& b) { return a.x < b.x; });
+    for (size_t e = 0; e < ents.size();) {
+      const int j = ents[e].x;
+      pr_col.push_back(j);
+      for (; e < ents.size() && ents[e].x == j; ++e) pr_ent.push_back(make_int2(4 * ents[e].y + ents[e].w, ents[e].z));
+      pr_cptr.push_back((int)pr_ent.size());
+    }
+    pr_ptr[k + 1] = (int)pr_col.size();
+  }
 
   Pool P;
   const size_t oW = P.add(W.data(), W.size() * 8), oiW = P.add(invW.data(), invW.size() * 8),
@@ -279,7 +291,8 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
                oS = P.add(slots.data(), slots.size() * sizeof(int4)), oR = P.add(rev.data(), rev.size() * 4),
                oF = P.add(fo.data(), fo.size() * 8), oE = P.add(eff.data(), eff.size() * 8),
                oSp = P.add(sp_ptr.data(), sp_ptr.size() * 4), oSe = P.add(sp_ent.data(), sp_ent.size() * 8),
-               oJp = P.add(jr_ptr.data(), jr_ptr.size() * 4), oJe = P.add(jr_ent.data(), jr_ent.size() * 16),
+               oPp = P.add(pr_ptr.data(), pr_ptr.size() * 4), oPc = P.add(pr_col.data(), pr_col.size() * 4),
+               oPq = P.add(pr_cptr.data(), pr_cptr.size() * 4), oPe = P.add(pr_ent.data(), pr_ent.size() * 8),
                oTp = P.add(tr_ptr.data(), tr_ptr.size() * 4), oTe = P.add(tr_ent.data(), tr_ent.size() * 8);
   CHEM_CUDA(h, cudaMalloc(&h->d_tables, P.host.size()));
   CHEM_CUDA(h, cudaMemcpy(h->d_tables, P.host.data(), P.host.size(), cudaMemcpyHostToDevice));
@@ -302,8 +315,10 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
   m.eff = reinterpret_cast<const double*>(b + oE);
   m.sp_ptr = reinterpret_cast<const int*>(b + oSp);
   m.sp_ent = reinterpret_cast<const int2*>(b + oSe);
-  m.jr_ptr = reinterpret_cast<const int*>(b + oJp);
-  m.jr_ent = reinterpret_cast<const int4*>(b + oJe);
+  m.pr_ptr = reinterpret_cast<const int*>(b + oPp);
+  m.pr_col = reinterpret_cast<const int*>(b + oPc);
+  m.pr_cptr = reinterpret_cast<const int*>(b + oPq);
+  m.pr_ent = reinterpret_cast<const int2*>(b + oPe);
   m.tr_ptr = reinterpret_cast<const int*>(b + oTp);
   m.tr_ent = reinterpret_cast<const int2*>(b + oTe);
   return CHEM_OK;
@@ -419,6 +434,7 @@ static const OptionDef kOptions[] = {
     {"ctas_per_sm", &chem_handle_s::ctas_per_sm, 0, 64},
     {"graph", &chem_handle_s::graph, 0, 1},
     {"autotune", &chem_handle_s::autotune, 0, 1},
+    {"profile", &chem_handle_s::profile, 0, 1},
 };
 
 extern "C" chem_status chem_set_option(chem_handle h, const char* key, double value) {
@@ -515,6 +531,15 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
   a.smem_I = std::max(Imax, 1);
   a.queue = static_cast<int*>(h0->d_queue);
   a.perm = nullptr;
+  a.phase = nullptr;
+  if (h0->profile) {
+    if (!h0->d_phase) {
+      chem_status ps = chem_internal_alloc(h0, &h0->d_phase, 8 * sizeof(unsigned long long));
+      if (ps != CHEM_OK) return ps;
+      CHEM_CUDA(h0, cudaMemsetAsync(h0->d_phase, 0, 8 * sizeof(unsigned long long), st));
+    }
+    a.phase = h0->d_phase;
+  }
   chem_status s = chem_internal_prepare_learned(h0, jobs, n_jobs, &a, st);
   if (s != CHEM_OK) return s;
   const size_t smem = smem_bytes(a.smem_K, a.smem_I, h0->precision);
@@ -675,6 +700,17 @@ extern "C" chem_status chem_get_totals(chem_handle h, void* stream, int64_t* n_c
 // ---------------------------------------------------------------------------
 // diagnostics
 // ---------------------------------------------------------------------------
+extern "C" chem_status chem_get_phase_cycles(chem_handle h, void* stream, uint64_t* cycles, int32_t reset) {
+  if (!h || !cycles) return CHEM_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int k = 0; k < 8; ++k) cycles[k] = 0;
+  if (!h->d_phase) return CHEM_OK;
+  CHEM_CUDA(h, cudaMemcpyAsync(cycles, h->d_phase, 8 * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+  if (reset) CHEM_CUDA(h, cudaMemsetAsync(h->d_phase, 0, 8 * sizeof(uint64_t), st));
+  CHEM_CUDA(h, cudaStreamSynchronize(st));
+  return CHEM_OK;
+}
+
 extern "C" chem_status chem_eval_rhs(chem_handle h, int64_t n, const double* T, const double* p,
                                      const double* Y, double* f, void* stream) {
   if (!h || n < 0 || (n > 0 && (!T || !p || !Y || !f))) return CHEM_ERR_INVALID_ARG;

@@ -22,7 +22,7 @@ struct chem_handle_s {
   std::vector<void*> allocations;   // every other device allocation of the handle
   // options
   int precision = chem::PREC_FP64;
-  int ir_sweeps = 2;
+  int ir_sweeps = 1;
   int scheduler = chem::SCHED_QUEUE;
   int order = 0;
   int h0mode = 0;
@@ -31,6 +31,8 @@ struct chem_handle_s {
   int ctas_per_sm = 0;
   int graph = 0;
   int autotune = 0;
+  int profile = 0;
+  unsigned long long* d_phase = nullptr;  // [8] per-phase cycle counters (option "profile")
   // per-cell statistics of the last call
   int64_t stats_cap = 0;
   int64_t last_n = 0;

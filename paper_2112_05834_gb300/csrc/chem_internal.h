@@ -42,12 +42,14 @@ struct DevMech {
   const int4* slots;    // [I]: reactant slot 0/1, product slot 0/1 species (-1 empty);
                         //      a coefficient of 2 appears as two equal slots
   const int* rev;       // [I] 0/1
-  const double* fo;     // [n_fo][8]: ln A0, b0, Ea0_R, alpha, T***, T*, T**, 0
+  const double* fo;     // [n_fo][8]: ln A0, b0, Ea0_R, alpha, 1/T***, 1/T*, T**, 0
   const double* eff;    // [n_tb][K] (row r belongs to reaction i_tb0 + r)
   const int* sp_ptr;    // [K+1] species -> (reaction, nu) CSR
   const int2* sp_ent;
-  const int* jr_ptr;    // [K+1] Jacobian row k -> (col j, reaction i, nu_ki, slot)
-  const int4* jr_ent;
+  const int* pr_ptr;    // [K+1] Jacobian row k -> its distinct mass-action columns q
+  const int* pr_col;    // [npairs] column j (species) of pair q
+  const int* pr_cptr;   // [npairs+1] pair q -> contributions
+  const int2* pr_ent;   // (4 i + slot, nu_ki): nu_ki dq_i/dC(slot) adds to (k, j)
   const int* tr_ptr;    // [K+1] row k -> (reaction i with [M], nu_ki)
   const int2* tr_ent;
 };
@@ -83,6 +85,7 @@ struct IntegrateArgs {
   int ir_sweeps;
   int use_h0;          // 1: take jobs[j].h0 when finite and positive
   int smem_K, smem_I;  // sizes the shared-memory carve-up was computed for
+  unsigned long long* phase;  // optional [8] per-phase cycle counters (diagnostic)
 };
 
 }  // namespace chem

@@ -68,7 +68,7 @@ struct Layout {
 __host__ __device__ inline int odd_ld(int n) { return n | 1; }
 
 // vectors (double): y, yn, ys, f0, fv, rr, u[6], sc  -> 13 n
-// species (double): C, hRT, cpR, eg, dcp, dk, akT, ek -> 8 K
+// species (double): C, hRT, cpR, eg, dcp, dk, akT, ek, ieg -> 9 K
 // reactions (double): q, D, dTc, P, dqs[4] -> 8 I
 __host__ __device__ inline Layout make_layout(int Kmax, int Imax, int prec) {
   Layout L;
@@ -82,7 +82,7 @@ __host__ __device__ inline Layout make_layout(int Kmax, int Imax, int prec) {
   L.off_vec = o;
   o += (size_t)13 * L.nmax * sizeof(double);
   L.off_sp = o;
-  o += (size_t)8 * Kmax * sizeof(double);
+  o += (size_t)9 * Kmax * sizeof(double);
   L.off_rx = o;
   o += (size_t)8 * Imax * sizeof(double);
   const size_t es = prec == PREC_FP64 ? sizeof(double) : sizeof(float);
@@ -104,7 +104,7 @@ __host__ __device__ inline Layout make_layout(int Kmax, int Imax, int prec) {
 size_t smem_bytes(int Kmax, int Imax, int prec) { return make_layout(Kmax, Imax, prec).total; }
 
 // Scalars kept in the reduction area (after the 4 x NW partial-sum slots).
-enum { SC_LOGT = 48, SC_INVP = 49, SC_FLAG = 50, SC_MISC = 51 };
+enum { SC_LOGT = 48, SC_INVP = 49, SC_FLAG = 50, SC_MISC = 51, SC_PIV = 52 };  // SC_PIV: 2 x NW slots
 
 template <int NW>
 struct Cta {
@@ -114,7 +114,7 @@ struct Cta {
   // vectors
   double *y, *yn, *ys, *f0, *fv, *rr, *u, *sc;
   // species
-  double *C, *hRT, *cpR, *eg, *dcp, *dk, *akT, *ek;
+  double *C, *hRT, *cpR, *eg, *dcp, *dk, *akT, *ek, *ieg;
   // reactions
   double *q, *D, *dTc, *P, *dqs;
   void* M;
@@ -147,6 +147,7 @@ struct Cta {
     dk = s + 5 * K;
     akT = s + 6 * K;
     ek = s + 7 * K;
+    ieg = s + 8 * K;
     double* r = reinterpret_cast<double*>(base + L.off_rx);
     const int I = L.Imax;
     q = r;
@@ -186,7 +187,7 @@ struct Cta {
 
 // Cell-level scalars shared by all threads of the CTA (identical in every thread).
 struct Scal {
-  double T, invT, logT, rho, Wbar, cpm, fT, dcpm, Scpw;
+  double T, invT, logT, rho, irho, Wbar, cpm, fT, dcpm, Scpw;
 };
 
 // ---------------------------------------------------------------------------
@@ -213,6 +214,7 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
     c.sum(part);
     s.Wbar = 1.0 / part[0];
     s.rho = p / (kRc * s.T * part[0]);
+    s.irho = kRc * s.T * part[0] / p;
   }
   s.logT = c.red[SC_LOGT];
   const double T = s.T, invT = s.invT, logT = s.logT;
@@ -225,12 +227,15 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
     double sr = a[11] * logT + T * (a[12] + T * (a[13] + T * (a[14] + T * a[15]))) + a[16];
     c.cpR[k] = cp;
     c.hRT[k] = h;
-    c.eg[k] = exp(h - sr);
+    const double e = exp(h - sr);
+    c.eg[k] = e;
+    c.ieg[k] = 1.0 / e;
     c.C[k] = s.rho * y[1 + k] * m.invW[k];
     if (JAC) c.dcp[k] = a[1] + T * (2.0 * a[2] + T * (3.0 * a[3] + T * 4.0 * a[4]));
   }
   __syncthreads();
   const double cRT = kRc * T / kP0;  // (P0 / (Rc T))^-1
+  const double icRT = kP0 * invT / kRc;
   for (int i = c.tid; i < I; i += NT) {
     const double* arp = m.arr + 4 * i;
     const double2 a01 = reinterpret_cast<const double2*>(arp)[0];
@@ -246,11 +251,11 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
     // 1/Kc = exp(dG/RT) (Rc T/P0)^dnu with exp(dG/RT) from the species factors
     double ratio = 0.0;
     if (m.rev[i]) {
-      double num = c.eg[sl.z] * (sl.w >= 0 ? c.eg[sl.w] : 1.0);
-      double den = c.eg[sl.x] * (sl.y >= 0 ? c.eg[sl.y] : 1.0);
-      ratio = num / den;
+      ratio = c.eg[sl.z] * c.ieg[sl.x];
+      if (sl.w >= 0) ratio *= c.eg[sl.w];
+      if (sl.y >= 0) ratio *= c.ieg[sl.y];
       if (ar.w > 0.5) ratio *= cRT;
-      else if (ar.w < -0.5) ratio /= cRT;
+      else if (ar.w < -0.5) ratio *= icRT;
     }
     double Mc = 0.0, phi = 1.0;
     double dk_dM = 0.0, dlnk = ar.y * invT + ar.z * invT * invT, dk_dT = 0.0;
@@ -268,9 +273,10 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
       double F = 1.0, dF_dPr = 0.0, dF_dT = 0.0;
       if (i >= m.i_troe0) {
         const double alpha = fo[3];
-        const double e3 = exp(-T / fo[4]), e1 = exp(-T / fo[5]);
+        // fo[4] = 1/T***, fo[5] = 1/T*
+        const double e3 = exp(-T * fo[4]), e1 = exp(-T * fo[5]);
         double Fc = (1.0 - alpha) * e3 + alpha * e1;
-        double dFc = -(1.0 - alpha) / fo[4] * e3 - alpha / fo[5] * e1;
+        double dFc = -(1.0 - alpha) * fo[4] * e3 - alpha * fo[5] * e1;
         if (fo[6] > 0.0) {
           const double e2 = exp(-fo[6] * invT);
           Fc += e2;
@@ -351,7 +357,7 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
         at += nu * c.dTc[en.x];
       }
     }
-    f[1 + k] = m.W[k] * w / s.rho;
+    f[1 + k] = m.W[k] * w * s.irho;
     part[0] += c.hRT[k] * w;                  // Qh / (Rc T)
     part[1] += y[1 + k] * c.cpR[k] * m.invW[k];  // cpm / Rc
     if (JAC) {
@@ -375,8 +381,11 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
 }
 
 // ---------------------------------------------------------------------------
-// Jacobian assembly (precision R) from the data of eval_rhs<JAC=true>.
-// Writes J (jac_only) or the iteration matrix M = I/(h gamma) - J into c.M.
+// Jacobian assembly (precision R) from the data of eval_rhs<JAC=true>, one warp per
+// species row: dense third-body/falloff part, sparse mass-action part (per-(row,
+// column) contribution lists, fixed order), rank-one density terms and the
+// temperature column; then the temperature row from column sums. Writes the
+// iteration matrix M = I/(h gamma) - J (fac > 0), or J itself (jac_only).
 // ---------------------------------------------------------------------------
 template <int NW, class R>
 __device__ void assemble(const DevMech& m, Cta<NW>& c, const Scal& s, const double* y, const double* f,
@@ -384,10 +393,15 @@ __device__ void assemble(const DevMech& m, Cta<NW>& c, const Scal& s, const doub
   constexpr int NT = NW * 32;
   const int K = m.K, n = K + 1, ld = odd_ld(n);
   R* A = reinterpret_cast<R*>(target);
+  // stored value S = sg J + fac I  (sg = -1: iteration matrix; sg = +1, fac = 0: Jacobian)
+  const R sg = jac_only ? R(1) : R(-1);
+  const R rf = jac_only ? R(0) : R(fac);
   // e_k = h_k / (W_k cp) with the molar enthalpy h_k = hRT_k Rc T
   for (int k = c.tid; k < K; k += NT) c.ek[k] = c.hRT[k] * kRc * s.T * m.invW[k] / s.cpm;
-  // (1) dense third-body / falloff part of A_kj = sum_i nu_ki dq_i/dC_j
+  const R wr = R(s.Wbar / s.rho), wb = R(s.Wbar);
   for (int k = c.warp; k < K; k += NW) {
+    R* row = A + (1 + k) * ld + 1;
+    // (1) third-body / falloff part of A_kj = sum_i nu_ki dq_i/dC_j: sum_i nu_ki P_i eff_ij
     const int t0 = m.tr_ptr[k], t1 = m.tr_ptr[k + 1];
     for (int j = c.lane; j < K; j += 32) {
       R a = R(0);
@@ -395,96 +409,114 @@ __device__ void assemble(const DevMech& m, Cta<NW>& c, const Scal& s, const doub
         const int2 en = m.tr_ent[t];
         a += R(en.y) * R(c.P[en.x]) * R(m.eff[(size_t)(en.x - m.i_tb0) * K + j]);
       }
-      A[(1 + k) * ld + 1 + j] = a;
+      row[j] = a;
     }
-  }
-  __syncthreads();
-  // (2) sparse mass-action part, one thread per row
-  for (int k = c.tid; k < K; k += NT) {
-    R* row = A + (1 + k) * ld + 1;
-    for (int e = m.jr_ptr[k]; e < m.jr_ptr[k + 1]; ++e) {
-      const int4 en = m.jr_ent[e];
-      row[en.x] += R(en.z) * R(c.dqs[4 * en.y + en.w]);
+    __syncwarp();
+    // (2) mass-action part: one lane per distinct column of the row
+    for (int q = m.pr_ptr[k] + c.lane; q < m.pr_ptr[k + 1]; q += 32) {
+      R a = R(0);
+      for (int e = m.pr_cptr[q]; e < m.pr_cptr[q + 1]; ++e) {
+        const int2 en = m.pr_ent[e];
+        a += R(en.y) * R(c.dqs[en.x]);
+      }
+      row[m.pr_col[q]] += a;
     }
-  }
-  __syncthreads();
-  // (3) species block and T column:
-  //   J_kj = (W_k/W_j) (A_kj - (Wbar/rho) d_k) + f_k Wbar / W_j
-  //   J_k0 = (W_k/rho) (a_kT - d_k / T) + f_k / T
-  const R wr = R(s.Wbar / s.rho), wb = R(s.Wbar);
-  for (int k = c.warp; k < K; k += NW) {
+    __syncwarp();
+    // (3) J_kj = (W_k/W_j) (A_kj - (Wbar/rho) d_k) + f_k Wbar / W_j;
+    //     J_k0 = (W_k/rho) (a_kT - d_k / T) + f_k / T
     const R Wk = R(m.W[k]), dk = R(c.dk[k]), fk = R(f[1 + k]);
-    R* row = A + (1 + k) * ld + 1;
     for (int j = c.lane; j < K; j += 32) {
       const R iW = R(m.invW[j]);
-      row[j] = Wk * iW * (row[j] - wr * dk) + fk * wb * iW;
+      const R J = Wk * iW * (row[j] - wr * dk) + fk * wb * iW;
+      row[j] = sg * J + (j == k ? rf : R(0));
     }
     if (c.lane == 0)
-      A[(1 + k) * ld] = R(m.W[k] / s.rho * (c.akT[k] - c.dk[k] * s.invT) + f[1 + k] * s.invT);
+      row[-1] = sg * R(m.W[k] * s.irho * (c.akT[k] - c.dk[k] * s.invT) + f[1 + k] * s.invT);
   }
   __syncthreads();
   // (4) temperature row: J_0j = -sum_k e_k J_kj - f_T cp_j / (W_j cp);
-  //     J_00 = -sum_k e_k J_k0 - sum_k cp_k omega_k / (rho cp) - f_T cp'/cp
+  //     J_00 = -sum_k e_k J_k0 - sum_k cp_k omega_k / (rho cp) - f_T cp'/cp,
+  //     with J_kj = sg (S_kj - fac delta) read back from the stored values
   for (int j = c.tid; j < n; j += NT) {
     R acc = R(0);
     for (int k = 0; k < K; ++k) acc += R(c.ek[k]) * A[(1 + k) * ld + j];
+    if (j >= 1) acc -= rf * R(c.ek[j - 1]);
+    acc *= sg;
     R extra;
     if (j == 0)
-      extra = R(s.Scpw / (s.rho * s.cpm) + s.fT * s.dcpm / s.cpm);
+      extra = R(s.Scpw * s.irho / s.cpm + s.fT * s.dcpm / s.cpm);
     else
       extra = R(s.fT * c.cpR[j - 1] * kRc * m.invW[j - 1] / s.cpm);
-    A[j] = -acc - extra;
+    A[j] = sg * (-acc - extra) + (j == 0 ? rf : R(0));
   }
-  __syncthreads();
-  if (jac_only) return;
-  // (5) M = I/(h gamma) - J
-  const R rf = R(fac);
-  for (int i = c.warp; i < n; i += NW)
-    for (int j = c.lane; j < n; j += 32) {
-      R v = -A[i * ld + j];
-      if (i == j) v += rf;
-      A[i * ld + j] = v;
-    }
   __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
-// dense LU with partial pivoting (row interchanges to the largest |a_ik|, lowest
-// row index on ties), in place; then the composed row permutation and the inverse
-// diagonal of U for the solves. Returns 0 or 1 + k for a zero pivot at column k.
+// Pivot candidates: every warp writes (max |value|, lowest row index) of its rows;
+// every thread then reduces the NW partials in the same order (same result).
+// ---------------------------------------------------------------------------
+template <int NW>
+__device__ __forceinline__ int pivot_reduce(Cta<NW>& c, float* pmax, int* pidx, int n) {
+  float best = -1.0f;
+  int bi = n;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const float v = pmax[w];
+    const int i = pidx[w];
+    if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+  }
+  return bi;
+}
+
+// Warp-level (value, index) maximum with the lowest index on ties; lane 0 stores it.
+__device__ __forceinline__ void warp_argmax_store(float v, int i, int lane, float* pmax, int* pidx, int warp) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const float ov = __shfl_xor_sync(FULLMASK, v, o);
+    const int oi = __shfl_xor_sync(FULLMASK, i, o);
+    if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
+  }
+  if (lane == 0) {
+    pmax[warp] = v;
+    pidx[warp] = i;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// dense LU with partial pivoting (row interchange to the largest |a_ik|, lowest
+// row index on ties; the pivot choice compares magnitudes rounded to FP32), in
+// place; the search for the next pivot is fused into the elimination, so each
+// column costs two CTA barriers. Then the composed row permutation and the
+// inverse diagonal of U for the solves. Returns 0 or 1 + k for a zero pivot.
 // ---------------------------------------------------------------------------
 template <int NW, class R>
 __device__ int lu_factor(Cta<NW>& c, R* a, int n) {
   constexpr int NT = NW * 32;
   const int ld = odd_ld(n);
+  float* pmax = reinterpret_cast<float*>(c.red + SC_PIV);
+  int* pidx = reinterpret_cast<int*>(c.red + SC_PIV + NW);
+  double* spinv = c.red + SC_INVP;
   int info = 0;
-  for (int k = 0; k < n; ++k) {
-    if (c.warp == 0) {
-      double best = -1.0;
-      int bi = n;
-      for (int i = k + c.lane; i < n; i += 32) {
-        const double v = fabs((double)a[i * ld + k]);
-        if (v > best) { best = v; bi = i; }
-      }
-#pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        const double ov = __shfl_xor_sync(FULLMASK, best, o);
-        const int oi = __shfl_xor_sync(FULLMASK, bi, o);
-        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-      }
-      if (c.lane == 0) {
-        if (bi >= n) {  // the whole column is NaN: report a zero pivot, keep k
-          bi = k;
-          best = 0.0;
-        }
-        c.piv[k] = bi;
-        c.red[SC_INVP] = best > 0.0 ? 1.0 / (double)a[bi * ld + k] : 0.0;
-      }
+  // candidates for column 0
+  {
+    float v = -1.0f;
+    int bi = n;
+    for (int i = c.tid; i < n; i += NT) {
+      const float x = fabsf((float)a[i * ld]);
+      if (x > v || (x == v && i < bi)) { v = x; bi = i; }
     }
-    __syncthreads();
-    const int p = c.piv[k];
-    const R invp = R(c.red[SC_INVP]);
-    if (invp == R(0) && info == 0) info = k + 1;
+    warp_argmax_store(v, bi, c.lane, pmax, pidx, c.warp);
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    int p = pivot_reduce<NW>(c, pmax, pidx, n);
+    if (p >= n) p = k;  // a column of NaN: the zero-pivot path below
+    if (c.tid == 0) {
+      c.piv[k] = p;
+      const double pv = (double)a[p * ld + k];
+      spinv[0] = pv != 0.0 && isfinite(pv) ? 1.0 / pv : 0.0;
+    }
     if (p != k)
       for (int j = c.tid; j < n; j += NT) {
         const R t = a[k * ld + j];
@@ -492,12 +524,24 @@ __device__ int lu_factor(Cta<NW>& c, R* a, int n) {
         a[p * ld + j] = t;
       }
     __syncthreads();
+    const R invp = R(spinv[0]);
+    if (invp == R(0) && info == 0) info = k + 1;
+    float v = -1.0f;
+    int bi = n;
     for (int i = k + 1 + c.warp; i < n; i += NW) {
       const R l = a[i * ld + k] * invp;
       __syncwarp();
       if (c.lane == 0) a[i * ld + k] = l;
-      for (int j = k + 1 + c.lane; j < n; j += 32) a[i * ld + j] -= l * a[k * ld + j];
+      for (int j = k + 1 + c.lane; j < n; j += 32) {
+        const R nv = a[i * ld + j] - l * a[k * ld + j];
+        a[i * ld + j] = nv;
+        if (j == k + 1) {
+          const float x = fabsf((float)nv);
+          if (x > v || (x == v && i < bi)) { v = x; bi = i; }
+        }
+      }
     }
+    warp_argmax_store(v, bi, c.lane, pmax, pidx, c.warp);
     __syncthreads();
   }
   // composed permutation: position i of the pivoted system holds original row perm[i]
@@ -556,9 +600,85 @@ __device__ void lu_solve_warp(const R* a, int n, const double* invd, R* x, int l
   }
 }
 
+// In-place Gauss-Jordan inverse (FP32) with partial pivoting: row interchange to
+// the largest |a_ik| (lowest row index on ties), the normalised pivot row kept in a
+// copy while every other row is eliminated (the next pivot search is fused into
+// that elimination: two CTA barriers per column); the inverse is completed by the
+// column interchanges in reverse order. Returns 0 or 1 + k for a zero pivot.
+template <int NW>
+__device__ int gj_invert(Cta<NW>& c, float* a, int n) {
+  constexpr int NT = NW * 32;
+  const int ld = odd_ld(n);
+  float* pmax = reinterpret_cast<float*>(c.red + SC_PIV);
+  int* pidx = reinterpret_cast<int*>(c.red + SC_PIV + NW);
+  float* pr = reinterpret_cast<float*>(c.rr);  // normalised pivot row
+  int info = 0;
+  {
+    float v = -1.0f;
+    int bi = n;
+    for (int i = c.tid; i < n; i += NT) {
+      const float x = fabsf(a[i * ld]);
+      if (x > v || (x == v && i < bi)) { v = x; bi = i; }
+    }
+    warp_argmax_store(v, bi, c.lane, pmax, pidx, c.warp);
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    int p = pivot_reduce<NW>(c, pmax, pidx, n);
+    if (p >= n) p = k;
+    const float pv = a[p * ld + k];
+    const float pinv = (pv != 0.0f && isfinite(pv)) ? 1.0f / pv : 0.0f;
+    if (pinv == 0.0f && info == 0) info = k + 1;
+    if (c.tid == 0) c.piv[k] = p;
+    // interchange rows k and p; the new row k, normalised, goes to the copy
+    for (int j = c.tid; j < n; j += NT) {
+      const float rk = a[k * ld + j], rp = a[p * ld + j];
+      if (p != k) a[p * ld + j] = rk;
+      pr[j] = (j == k ? 1.0f : rp) * pinv;
+    }
+    __syncthreads();
+    const int cn = k + 1;              // next pivot column
+    const int own = cn & 31;           // lane owning column cn in the loops below
+    float v = -1.0f;
+    int bi = n;
+    for (int i = c.warp; i < n; i += NW) {
+      if (i == k) {
+        for (int j = c.lane; j < n; j += 32) a[k * ld + j] = pr[j];
+        continue;
+      }
+      const float fct = a[i * ld + k];
+      __syncwarp();
+      for (int j = c.lane; j < n; j += 32) {
+        const float nv = (j == k ? 0.0f : a[i * ld + j]) - fct * pr[j];
+        a[i * ld + j] = nv;
+        if (j == cn && i > k) {
+          const float x = fabsf(nv);
+          if (x > v || (x == v && i < bi)) { v = x; bi = i; }
+        }
+      }
+    }
+    (void)own;
+    warp_argmax_store(v, bi, c.lane, pmax, pidx, c.warp);
+    __syncthreads();
+  }
+  // column interchanges in reverse order; each thread owns whole rows
+  for (int i = c.tid; i < n; i += NT)
+    for (int k = n - 1; k >= 0; --k) {
+      const int p = c.piv[k];
+      if (p != k) {
+        const float t = a[i * ld + k];
+        a[i * ld + k] = a[i * ld + p];
+        a[i * ld + p] = t;
+      }
+    }
+  __syncthreads();
+  return info;
+}
+
 // Solve M x = b for the FP64 right-hand side b; x written as double.
-// FP64: plain LU solve. Otherwise: FP32 solve, then `ir` sweeps of
-// r = b - M0 x (accumulated in FP64 against the assembled matrix M0), x += M^-1 r.
+// FP64: LU forward/back substitution. Otherwise: x = M32^-1 b with the FP32
+// inverse, then `ir` sweeps of r = b - M0 x (FP64, against the assembled matrix
+// M0) and x += M32^-1 r. One thread per row in every matrix-vector product.
 template <int NW, int PREC>
 __device__ void solve(Cta<NW>& c, int n, const double* b, double* x, int ir) {
   constexpr int NT = NW * 32;
@@ -569,32 +689,45 @@ __device__ void solve(Cta<NW>& c, int n, const double* b, double* x, int ir) {
     if (c.warp == 0) lu_solve_warp<double>(reinterpret_cast<double*>(c.M), n, c.invd, x, c.lane);
     __syncthreads();
   } else {
-    const float* a = reinterpret_cast<const float*>(c.M);
+    const float* Ai = reinterpret_cast<const float*>(c.M);
     const typename P::ASM* M0 = reinterpret_cast<const typename P::ASM*>(c.M0);
     float* xf = reinterpret_cast<float*>(c.sc);  // scratch vector reused as float
-    for (int i = c.tid; i < n; i += NT) xf[i] = (float)b[c.perm[i]];
-    __syncthreads();
-    if (c.warp == 0) lu_solve_warp<float>(a, n, c.invd, xf, c.lane);
-    __syncthreads();
-    for (int i = c.tid; i < n; i += NT) x[i] = (double)xf[i];
-    __syncthreads();
     const int ld = odd_ld(n);
+    for (int i = c.tid; i < n; i += NT) xf[i] = (float)b[i];
+    __syncthreads();
+    for (int i = c.tid; i < n; i += NT) {
+      float acc = 0.0f;
+      const float* row = Ai + i * ld;
+      for (int j = 0; j < n; ++j) acc = fmaf(row[j], xf[j], acc);
+      x[i] = (double)acc;
+    }
+    __syncthreads();
     for (int sweep = 0; sweep < ir; ++sweep) {
-      for (int i = c.warp; i < n; i += NW) {
-        double acc = 0.0;
-        for (int j = c.lane; j < n; j += 32) acc += (double)M0[i * ld + j] * x[j];
-#pragma unroll
-        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(FULLMASK, acc, o);
-        if (c.lane == 0) c.rr[i] = b[i] - acc;
+      for (int i = c.tid; i < n; i += NT) {
+        double acc = b[i];
+        const typename P::ASM* row = M0 + i * ld;
+        for (int j = 0; j < n; ++j) acc -= (double)row[j] * x[j];
+        xf[i] = (float)acc;
       }
       __syncthreads();
-      for (int i = c.tid; i < n; i += NT) xf[i] = (float)c.rr[c.perm[i]];
-      __syncthreads();
-      if (c.warp == 0) lu_solve_warp<float>(a, n, c.invd, xf, c.lane);
-      __syncthreads();
-      for (int i = c.tid; i < n; i += NT) x[i] += (double)xf[i];
+      for (int i = c.tid; i < n; i += NT) {
+        float acc = 0.0f;
+        const float* row = Ai + i * ld;
+        for (int j = 0; j < n; ++j) acc = fmaf(row[j], xf[j], acc);
+        x[i] += (double)acc;
+      }
       __syncthreads();
     }
+  }
+}
+
+// Factorisation of the iteration matrix: LU (FP64 form) or the FP32 inverse.
+template <int NW, int PREC>
+__device__ int factor(Cta<NW>& c, int n) {
+  if constexpr (!Policy<PREC>::IR) {
+    return lu_factor<NW, double>(c, reinterpret_cast<double*>(c.M), n);
+  } else {
+    return gj_invert<NW>(c, reinterpret_cast<float*>(c.M), n);
   }
 }
 
@@ -679,9 +812,25 @@ __device__ void h_cp_mass(const DevMech& m, Cta<NW>& c, double T, const double* 
 // ---------------------------------------------------------------------------
 // one cell
 // ---------------------------------------------------------------------------
+// Per-phase cycle counters (diagnostic; thread 0 reads the clock right after the
+// CTA barriers that close each phase): 0 load + starting step, 1 RHS and Jacobian
+// data at the step point, 2 iteration-matrix assembly, 3 factorisation, 4 stage RHS,
+// 5 stage solves, 6 stage combination + error norm + control, 7 T recovery + store.
+#define PHASE(k)                                                              \
+  do {                                                                        \
+    if (prof) {                                                               \
+      const long long now_ = clock64();                                       \
+      atomicAdd(args.phase + cur_, (unsigned long long)(now_ - last_));       \
+      last_ = now_;                                                           \
+      cur_ = (k);                                                             \
+    }                                                                         \
+  } while (0)
+
 template <int NW, int PREC>
 __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs& args, Cta<NW>& c) {
-  using R = typename Policy<PREC>::LU;
+  const bool prof = args.phase != nullptr && c.tid == 0;
+  long long last_ = prof ? clock64() : 0;
+  int cur_ = 0;
   constexpr int NT = NW * 32;
   const DevMech& m = job.m;
   const int K = m.K, n = K + 1;
@@ -715,17 +864,20 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
     }
     double t = 0.0;
     bool after_reject = false;
-    R* Mm = reinterpret_cast<R*>(c.M);
     while (true) {
       if (dt - t <= 1e-12 * dt) break;
       if (steps >= args.max_steps) { status = CHEM_CELL_MAX_STEPS; break; }
       if (!(h >= kHmin)) { status = CHEM_CELL_H_UNDERFLOW; break; }  // also catches NaN
       if (t + h > dt) h = dt - t;
       ++steps;
-      // Jacobian and f0 at y; iteration matrix; LU
+      // Jacobian and f0 at y; iteration matrix; factorisation
+      PHASE(1);
       const Scal s = eval_rhs<NW, true>(m, c, c.y, p, c.f0);
+      PHASE(2);
       build_matrix<NW, PREC>(m, c, s, c.y, c.f0, 1.0 / (h * kRodasGamma), false);
-      const int info = lu_factor<NW, R>(c, Mm, n);
+      PHASE(3);
+      const int info = factor<NW, PREC>(c, n);
+      PHASE(6);
       double err;
       if (info != 0) {
         err = NAN;
@@ -735,15 +887,18 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
         for (int st = 0; st < 6; ++st) {
           const double* fs = c.f0;
           if (st > 0) {
+            PHASE(6);
             for (int i = c.tid; i < n; i += NT) {
               double v = c.y[i];
               for (int j = 0; j < st; ++j) v += c_rodasA[st][j] * c.u[j * n + i];
               c.ys[i] = v;
             }
             __syncthreads();
+            PHASE(4);
             eval_rhs<NW, false>(m, c, c.ys, p, c.fv);
             fs = c.fv;
           }
+          PHASE(6);
           for (int i = c.tid; i < n; i += NT) {
             double v = fs[i];
             for (int j = 0; j < st; ++j) v += c_rodasC[st][j] * invh * c.u[j * n + i];
@@ -753,8 +908,10 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
           // rr is also the IR residual buffer: copy the stage RHS to fv first
           for (int i = c.tid; i < n; i += NT) c.fv[i] = c.rr[i];
           __syncthreads();
+          PHASE(5);
           solve<NW, PREC>(c, n, c.fv, c.u + st * n, args.ir_sweeps);
         }
+        PHASE(6);
         for (int i = c.tid; i < n; i += NT) {
           double v = c.y[i];
 #pragma unroll
@@ -781,6 +938,7 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
       h *= fac;
     }
     // temperature from the conserved mass enthalpy (Newton, |dT| < 1e-10 T)
+    PHASE(7);
     if (status == CHEM_CELL_OK) {
       double T = c.y[0];
       for (int it = 0; it < 50; ++it) {
@@ -800,6 +958,7 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
     if (c.tid == 0) job.T[cell] = c.y[0];
     for (int k = c.tid; k < K; k += NT) job.Y[(size_t)cell * K + k] = c.y[1 + k];
   }
+  PHASE(7);
   if (c.tid == 0) {
     if (job.st.substeps) job.st.substeps[cell] = steps;
     if (job.st.rejects) job.st.rejects[cell] = rejects;
@@ -912,7 +1071,7 @@ __global__ void __launch_bounds__(NW * 32) k_lu_solve(const __grid_constant__ Lu
       }
     for (int i = c.tid; i < n; i += NT) c.fv[i] = a.b[(size_t)s * n + i];
     __syncthreads();
-    const int info = lu_factor<NW, R>(c, M, n);
+    const int info = factor<NW, PREC>(c, n);
     if (info == 0) solve<NW, PREC>(c, n, c.fv, c.u, a.ir);
     for (int i = c.tid; i < n; i += NT) a.x[(size_t)s * n + i] = info == 0 ? c.u[i] : NAN;
     if (c.tid == 0 && a.info) a.info[s] = info;

@@ -132,3 +132,44 @@ def test_learned_form_gain_and_parity(pkg):
           "speed-up %.3f" % (out["plain"]["time"] / out["learned"]["time"]))
     assert out["learned"]["substeps"].sum() <= 1.02 * out["plain"]["substeps"].sum()
     assert rhs_learned < rhs_plain
+
+
+def test_cfd_loop_learned(pkg):
+    """A CFD-like sequence on the 100-species mechanism: between steps T += U[-50, 50] K
+    and Y mixes with a random partner cell. Steps 1-3 run the plain heuristic and log;
+    the model trains on those logs; steps 4-6 use the learned order and initial step.
+    Every step's outputs match the oracle on sampled cells of that step's inputs."""
+    import oracle
+
+    oracle.build()
+    m, st, dt = synth.workload("c100_1m", n_cells=8192, state_seed=46)
+    integ = pkg.Integrator(m, precision=1, scheduler=2)
+    model = pkg.CostModel(m.n_species, seed=8)
+    logs = []
+    rng = np.random.default_rng(2)
+    for step in range(6):
+        T, p, Y = _dev(st.T), _dev(st.p), _dev(st.Y)
+        if step == 3:
+            Ts = torch.cat([l[0] for l in logs])
+            ps = torch.cat([l[1] for l in logs])
+            Ys = torch.cat([l[2] for l in logs])
+            sub = torch.cat([l[3] for l in logs])
+            hf = torch.cat([l[4] for l in logs])
+            losses = model.train(Ts, ps, Ys, sub, hf, epochs=20, batch=4096, lr=1e-3, seed=9)
+            assert losses[-1] < losses[0]
+            model.attach(integ)
+            integ.set_option("order", 1)
+            integ.set_option("h0", 1)
+        T_in, Y_in = T.clone(), Y.clone()
+        integ.integrate(T, p, Y, dt, RTOL, ATOL)
+        s = integ.stats(st.T.shape[0])
+        assert int((s["status"] != 0).sum()) == 0
+        if step < 3:
+            logs.append((T_in, p, Y_in, s["substeps"].clone(), s["h_first"].clone()))
+        pick = rng.choice(st.T.shape[0], 8, replace=False)
+        ref = oracle.integrate(m, st.T[pick], st.p[pick], st.Y[pick], dt, RTOL, ATOL)
+        Tg, Yg = T.cpu().numpy(), Y.cpu().numpy()
+        assert np.all(np.abs(Tg[pick] - ref["T"]) <= 1e-6 * ref["T"]), step
+        assert np.all(np.abs(Yg[pick] - ref["Y"]) <= 1e-8 + 1e-5 * np.abs(ref["Y"])), step
+        print("step", step + 1, "substeps", int(s["substeps"].sum()))
+        st = synth.perturb_states(synth.CellStates(T=Tg, p=st.p, Y=Yg, kind=st.kind), seed=100 + step)

@@ -323,3 +323,22 @@ def test_full_size_sampled_parity(pkg, orc):
     ref = orc.integrate(m, st.T[pick], st.p[pick], st.Y[pick], dt, RTOL, ATOL)
     _assert_bound(g["T"][pick], g["Y"][pick], ref, "c54 full size")
     np.testing.assert_allclose(g["Y"].sum(axis=1), 1.0, atol=1e-10)
+
+
+@pytest.mark.parametrize("ir", [1, 2, 3])
+def test_full_size_c100_mixed_sampled_parity(pkg, orc, ir):
+    """100-species / 520-reaction mechanism, 262,144 cells at 40 bar in the mixed form
+    with 1, 2 and 3 refinement sweeps; sampled cells against the oracle."""
+    m, st, dt = synth.workload("c100_262k")
+    g = _run(pkg, m, st, dt, precision=1, scheduler=2, ir_sweeps=ir)
+    assert np.all(g["status"] == 0)
+    rng = np.random.default_rng(ir)
+    pick = []
+    for k in range(3):
+        idx = np.flatnonzero(st.kind == k)
+        pick.extend(rng.choice(idx, 6, replace=False))
+    pick.extend(np.argsort(g["substeps"])[-6:])
+    pick = np.unique(np.array(pick))
+    ref = orc.integrate(m, st.T[pick], st.p[pick], st.Y[pick], dt, RTOL, ATOL)
+    _assert_bound(g["T"][pick], g["Y"][pick], ref, f"c100 full size ir={ir}")
+    print(f"c100 262k ir={ir}: substeps {g['substeps'].sum()}")
