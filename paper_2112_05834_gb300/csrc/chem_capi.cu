@@ -195,18 +195,54 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
     }
     nasa[36 * k + 34] = d->T_mid[k];
   }
-  std::vector<double> arr((size_t)4 * I), fo, eff;
-  std::vector<int4> slots(I);
-  std::vector<int> rev(I);
+  // Each kind group is padded with null reactions to whole 32-reaction chunks, so a
+  // warp's chunk never mixes kinds; chunks are dealt to warps by decreasing cost.
+  std::vector<int> padded;
+  std::vector<double> chunk_cost;
+  for (int kind = 0; kind < 4; ++kind) {
+    size_t first = padded.size();
+    for (int i = 0; i < I; ++i)
+      if (d->rxn_type[order[i]] == kind) padded.push_back(order[i]);
+    if (padded.size() == first) continue;
+    while (padded.size() % 32) padded.push_back(-1);
+    const double cost = (kind == 0 ? 1.0 : kind == 1 ? 1.0 : kind == 2 ? 3.0 : 6.0) + (kind ? K / 16.0 : 0.0);
+    for (size_t c = first; c < padded.size(); c += 32) chunk_cost.push_back(cost);
+  }
+  const int Ip = (int)padded.size();
+  std::vector<int> chunk_order(chunk_cost.size());
+  std::iota(chunk_order.begin(), chunk_order.end(), 0);
+  std::stable_sort(chunk_order.begin(), chunk_order.end(),
+                   [&](int a, int b) { return chunk_cost[a] > chunk_cost[b]; });
+  h->rxn_order = padded;
+  std::vector<double> arr((size_t)4 * std::max(Ip, 1), 0.0), fo, eff;
+  std::vector<int4> slots(std::max(Ip, 1), make_int4(-1, -1, -1, -1));
+  std::vector<int> rev(std::max(Ip, 1), 0);
   std::vector<std::vector<int2>> sp(K), tr(K);
   std::vector<std::vector<int4>> jr(K);
-  int n_tb = 0, n_fo = 0, i_tb0 = I, i_fo0 = I, i_troe0 = I;
-  for (int i = 0; i < I; ++i) {
-    const int o = order[i];
-    const int t = d->rxn_type[o];
-    if (t >= 1 && i_tb0 == I) i_tb0 = i;
-    if (t >= 2 && i_fo0 == I) i_fo0 = i;
-    if (t == 3 && i_troe0 == I) i_troe0 = i;
+  int n_tb = 0, n_fo = 0, i_tb0 = Ip, i_fo0 = Ip, i_troe0 = Ip;
+  // kind of each padded position (null entries take the kind of their group)
+  std::vector<int> pkind(Ip);
+  for (int i = 0, last = 0; i < Ip; ++i) {
+    if (padded[i] >= 0) last = d->rxn_type[padded[i]];
+    pkind[i] = last;
+  }
+  for (int i = 0; i < Ip; ++i) {
+    const int o = padded[i];
+    const int t = pkind[i];
+    if (t >= 1 && i_tb0 == Ip) i_tb0 = i;
+    if (t >= 2 && i_fo0 == Ip) i_fo0 = i;
+    if (t == 3 && i_troe0 == Ip) i_troe0 = i;
+    if (o < 0) {  // null reaction: zero rows keep the per-kind tables aligned
+      if (t >= 1) {
+        ++n_tb;
+        eff.insert(eff.end(), K, 0.0);
+      }
+      if (t >= 2) {
+        ++n_fo;
+        fo.insert(fo.end(), 8, 0.0);
+      }
+      continue;
+    }
     int sl[4] = {-1, -1, -1, -1};
     int dnu = 0;
     for (int side = 0; side < 2; ++side) {
@@ -285,6 +321,16 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
     pr_ptr[k + 1] = (int)pr_col.size();
   }
 
+  std::vector<double> sp_nu(sp_ent.size()), pr_nu(pr_ent.size()), tr_nu(tr_ent.size());
+  for (size_t e = 0; e < sp_ent.size(); ++e) sp_nu[e] = sp_ent[e].y;
+  for (size_t e = 0; e < pr_ent.size(); ++e) pr_nu[e] = pr_ent[e].y;
+  for (size_t e = 0; e < tr_ent.size(); ++e) tr_nu[e] = tr_ent[e].y;
+  std::vector<float> eff_ff(2 * eff.size());
+  for (size_t e = 0; e < eff.size(); ++e) {
+    const float h = (float)eff[e];
+    eff_ff[2 * e] = h;
+    eff_ff[2 * e + 1] = (float)(eff[e] - (double)h);
+  }
   Pool P;
   const size_t oW = P.add(W.data(), W.size() * 8), oiW = P.add(invW.data(), invW.size() * 8),
                oN = P.add(nasa.data(), nasa.size() * 8), oA = P.add(arr.data(), arr.size() * 8),
@@ -293,13 +339,19 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
                oSp = P.add(sp_ptr.data(), sp_ptr.size() * 4), oSe = P.add(sp_ent.data(), sp_ent.size() * 8),
                oPp = P.add(pr_ptr.data(), pr_ptr.size() * 4), oPc = P.add(pr_col.data(), pr_col.size() * 4),
                oPq = P.add(pr_cptr.data(), pr_cptr.size() * 4), oPe = P.add(pr_ent.data(), pr_ent.size() * 8),
-               oTp = P.add(tr_ptr.data(), tr_ptr.size() * 4), oTe = P.add(tr_ent.data(), tr_ent.size() * 8);
+               oTp = P.add(tr_ptr.data(), tr_ptr.size() * 4), oTe = P.add(tr_ent.data(), tr_ent.size() * 8),
+               oSn = P.add(sp_nu.data(), sp_nu.size() * 8), oPn = P.add(pr_nu.data(), pr_nu.size() * 8),
+               oTn = P.add(tr_nu.data(), tr_nu.size() * 8),
+               oCo = P.add(chunk_order.data(), chunk_order.size() * 4),
+               oEf = P.add(eff_ff.data(), eff_ff.size() * 4);
   CHEM_CUDA(h, cudaMalloc(&h->d_tables, P.host.size()));
   CHEM_CUDA(h, cudaMemcpy(h->d_tables, P.host.data(), P.host.size(), cudaMemcpyHostToDevice));
   unsigned char* b = static_cast<unsigned char*>(h->d_tables);
   DevMech& m = h->dm;
   m.K = K;
-  m.I = I;
+  m.I = Ip;
+  m.n_chunks = (int)chunk_order.size();
+  h->I = std::max(Ip, 1);
   m.n_tb = n_tb;
   m.n_fo = n_fo;
   m.i_tb0 = i_tb0;
@@ -321,6 +373,11 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
   m.pr_ent = reinterpret_cast<const int2*>(b + oPe);
   m.tr_ptr = reinterpret_cast<const int*>(b + oTp);
   m.tr_ent = reinterpret_cast<const int2*>(b + oTe);
+  m.sp_nu = reinterpret_cast<const double*>(b + oSn);
+  m.pr_nu = reinterpret_cast<const double*>(b + oPn);
+  m.tr_nu = reinterpret_cast<const double*>(b + oTn);
+  m.chunk_order = reinterpret_cast<const int*>(b + oCo);
+  m.eff_ff = reinterpret_cast<const chem::ff2*>(b + oEf);
   return CHEM_OK;
 }
 
@@ -341,6 +398,7 @@ extern "C" chem_status chem_create(const chem_mechanism_desc* desc, chem_handle*
   chem_handle h = new chem_handle_s();
   h->K = desc->n_species;
   h->I = desc->n_reactions;
+  h->I_user = desc->n_reactions;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
   if (e != cudaSuccess) {
@@ -472,7 +530,7 @@ extern "C" const char* chem_last_error(chem_handle h) {
   return h ? h->err.c_str() : g_create_error.c_str();
 }
 extern "C" int32_t chem_n_species(chem_handle h) { return h ? h->K : -1; }
-extern "C" int32_t chem_n_reactions(chem_handle h) { return h ? h->I : -1; }
+extern "C" int32_t chem_n_reactions(chem_handle h) { return h ? h->I_user : -1; }
 
 // ---------------------------------------------------------------------------
 // integration
@@ -715,7 +773,7 @@ extern "C" chem_status chem_eval_rhs(chem_handle h, int64_t n, const double* T, 
                                      const double* Y, double* f, void* stream) {
   if (!h || n < 0 || (n > 0 && (!T || !p || !Y || !f))) return CHEM_ERR_INVALID_ARG;
   if (n == 0) return CHEM_OK;
-  CHEM_CUDA(h, launch_diag(h->dm, n, T, p, Y, f, 0, 0, 0, 0, PREC_FP64, static_cast<cudaStream_t>(stream)));
+  CHEM_CUDA(h, launch_diag(h->dm, n, T, p, Y, f, 0, 0, 0, 0, h->precision, static_cast<cudaStream_t>(stream)));
   return CHEM_OK;
 }
 
@@ -731,7 +789,7 @@ extern "C" chem_status chem_eval_h0(chem_handle h, int64_t n, const double* T, c
                                     double dt, double rtol, double atol, double* h0, void* stream) {
   if (!h || n < 0 || (n > 0 && (!T || !p || !Y || !h0)) || bad_tol(dt, rtol, atol)) return CHEM_ERR_INVALID_ARG;
   if (n == 0) return CHEM_OK;
-  CHEM_CUDA(h, launch_diag(h->dm, n, T, p, Y, h0, dt, rtol, atol, 2, PREC_FP64, static_cast<cudaStream_t>(stream)));
+  CHEM_CUDA(h, launch_diag(h->dm, n, T, p, Y, h0, dt, rtol, atol, 2, h->precision, static_cast<cudaStream_t>(stream)));
   return CHEM_OK;
 }
 

@@ -15,7 +15,9 @@ struct chem_mlp_s;
 struct chem_handle_s {
   int device = 0;
   int num_sms = 1;
-  int K = 0, I = 0;
+  int K = 0;
+  int I = 0;       // reactions as stored on the device (kind groups padded to 32)
+  int I_user = 0;  // reactions of the caller's mechanism
   chem::DevMech dm{};
   void* d_tables = nullptr;
   std::vector<int> rxn_order;       // sorted reaction position -> caller's reaction index

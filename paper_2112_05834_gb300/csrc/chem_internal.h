@@ -7,6 +7,8 @@
 
 namespace chem {
 
+struct ff2;
+
 constexpr int kMaxJobs = 8;
 constexpr double kRc = 8.31446261815324e7;  // erg / (mol K)
 constexpr double kP0 = 1.01325e6;           // dyn / cm^2, standard state (1 atm)
@@ -26,7 +28,9 @@ enum RxnKind { RK_ELEM = 0, RK_TB = 1, RK_LIND = 2, RK_TROE = 3 };
 // Device-resident struct-of-arrays tables of one mechanism. Reactions are stored
 // sorted by kind; species keep the caller's order.
 struct DevMech {
-  int K, I;
+  int K, I;     // I counts null padding reactions (slot 0 = -1), see chunk_order
+  int n_chunks;            // I / 32
+  const int* chunk_order;  // [n_chunks] 32-reaction chunks by decreasing cost
   int n_tb;   // reactions with a third-body concentration (kinds 1..3)
   int n_fo;   // falloff reactions (kinds 2, 3)
   int i_tb0;  // first reaction of kind >= 1 (sorted order)
@@ -44,12 +48,16 @@ struct DevMech {
   const int* rev;       // [I] 0/1
   const double* fo;     // [n_fo][8]: ln A0, b0, Ea0_R, alpha, 1/T***, 1/T*, T**, 0
   const double* eff;    // [n_tb][K] (row r belongs to reaction i_tb0 + r)
+  const struct ff2* eff_ff;  // the same efficiencies as float-float pairs (hi, lo)
   const int* sp_ptr;    // [K+1] species -> (reaction, nu) CSR
   const int2* sp_ent;
+  const double* sp_nu;  // the same nu as doubles
   const int* pr_ptr;    // [K+1] Jacobian row k -> its distinct mass-action columns q
   const int* pr_col;    // [npairs] column j (species) of pair q
   const int* pr_cptr;   // [npairs+1] pair q -> contributions
   const int2* pr_ent;   // (4 i + slot, nu_ki): nu_ki dq_i/dC(slot) adds to (k, j)
+  const double* pr_nu;  // the same nu as doubles
+  const double* tr_nu;  // nu of the tr_ent entries as doubles
   const int* tr_ptr;    // [K+1] row k -> (reaction i with [M], nu_ki)
   const int2* tr_ent;
 };

@@ -30,6 +30,40 @@ namespace chem {
 
 #define FULLMASK 0xffffffffu
 
+// ---------------------------------------------------------------------------
+// Float-float arithmetic (a value is hi + lo with two FP32 numbers): error-free
+// products with FMA (Dekker/Ogita-Rump-Oishi style TwoProduct) and TwoSum
+// (Knuth) give about 44-48 significant bits on the FP32 pipe, which on GB300
+// runs ~60x faster than the FP64 pipe. Used by the mixed form for long sums of
+// products (third-body concentrations, refinement residuals).
+// ---------------------------------------------------------------------------
+struct ff2 {
+  float hi, lo;
+};
+__device__ __forceinline__ ff2 ff_split(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double ff_value(ff2 a) { return (double)a.hi + (double)a.lo; }
+// s + p (both float-float), renormalised
+__device__ __forceinline__ ff2 ff_add(ff2 a, ff2 b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  const float h = s + e;
+  return {h, e - (h - s)};
+}
+// a * b (both float-float); the lo * lo term is below the precision kept
+__device__ __forceinline__ ff2 ff_mul(ff2 a, ff2 b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float h = p + e;
+  return {h, e - (h - p)};
+}
+
 // Rosenbrock coefficients in constant memory (stages are indexed at run time).
 __constant__ double c_rodasA[6][6] = CHEM_RODAS_A;
 __constant__ double c_rodasC[6][6] = CHEM_RODAS_C;
@@ -84,10 +118,18 @@ __host__ __device__ inline Layout make_layout(int Kmax, int Imax, int prec) {
   L.off_sp = o;
   o += (size_t)9 * Kmax * sizeof(double);
   L.off_rx = o;
-  o += (size_t)8 * Imax * sizeof(double);
-  const size_t es = prec == PREC_FP64 ? sizeof(double) : sizeof(float);
-  L.off_M = o;
-  o += (size_t)L.nmax * L.ld * es;
+  if (prec == PREC_FP64) {
+    o += (size_t)8 * Imax * sizeof(double);
+    L.off_M = o;
+    o += (size_t)L.nmax * L.ld * sizeof(double);
+  } else {
+    // The FP32 factor matrix is written only after the assembly has consumed the
+    // per-reaction Jacobian data (everything after q), so it shares their space.
+    L.off_M = o + (size_t)Imax * sizeof(double);
+    const size_t jac = (size_t)7 * Imax * sizeof(double);
+    const size_t mat = (size_t)L.nmax * L.ld * sizeof(float);
+    o += (size_t)Imax * sizeof(double) + (jac > mat ? jac : mat);
+  }
   o = (o + 15) & ~(size_t)15;
   L.off_M0 = o;
   if (prec == PREC_MIXED) o += (size_t)L.nmax * L.ld * sizeof(double);
@@ -197,7 +239,7 @@ struct Scal {
 // Jacobian assembly needs: per reaction the slot derivatives dq/dC, dq/dT at
 // fixed C, sum_k C_k dq/dC_k (D), and the third-body/falloff coefficient P of
 // eff_j in dq/dC_j; per species d_k = sum_i nu_ki D_i and a_kT = sum nu dTc.
-template <int NW, bool JAC>
+template <int NW, bool JAC, bool FF = false>
 __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p, double* f) {
   constexpr int NT = NW * 32;
   const int K = m.K, I = m.I;
@@ -230,18 +272,35 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
     const double e = exp(h - sr);
     c.eg[k] = e;
     c.ieg[k] = 1.0 / e;
-    c.C[k] = s.rho * y[1 + k] * m.invW[k];
+    const double Ck = s.rho * y[1 + k] * m.invW[k];
+    c.C[k] = Ck;
+    // float-float copy of C for the third-body sums (the slot of d_k, which the
+    // Jacobian evaluation writes only after the reaction loop)
+    if (FF) reinterpret_cast<ff2*>(c.dk)[k] = ff_split(Ck);
     if (JAC) c.dcp[k] = a[1] + T * (2.0 * a[2] + T * (3.0 * a[3] + T * 4.0 * a[4]));
   }
   __syncthreads();
   const double cRT = kRc * T / kP0;  // (P0 / (Rc T))^-1
   const double icRT = kP0 * invT / kRc;
-  for (int i = c.tid; i < I; i += NT) {
+  // 32-reaction chunks of one kind each, dealt to warps in a snake over the
+  // cost-descending chunk order
+  for (int pos = 0; pos < m.n_chunks; ++pos) {
+    const int r = pos % (2 * NW);
+    if ((r < NW ? r : 2 * NW - 1 - r) != c.warp) continue;
+    const int i = m.chunk_order[pos] * 32 + c.lane;
+    const int4 sl = m.slots[i];
+    if (sl.x < 0) {  // null padding reaction
+      c.q[i] = 0.0;
+      if (JAC) {
+        c.D[i] = c.dTc[i] = c.P[i] = 0.0;
+        c.dqs[4 * i] = c.dqs[4 * i + 1] = c.dqs[4 * i + 2] = c.dqs[4 * i + 3] = 0.0;
+      }
+      continue;
+    }
     const double* arp = m.arr + 4 * i;
     const double2 a01 = reinterpret_cast<const double2*>(arp)[0];
     const double2 a23 = reinterpret_cast<const double2*>(arp)[1];
     const struct { double x, y, z, w; } ar = {a01.x, a01.y, a23.x, a23.y};
-    const int4 sl = m.slots[i];
     double kf = exp(ar.x + ar.y * logT - ar.z * invT);
     const double Ca = c.C[sl.x];
     const double Cb = sl.y >= 0 ? c.C[sl.y] : 1.0;
@@ -261,7 +320,15 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
     double dk_dM = 0.0, dlnk = ar.y * invT + ar.z * invT * invT, dk_dT = 0.0;
     if (i >= m.i_tb0) {
       const double* e = m.eff + (size_t)(i - m.i_tb0) * K;
-      for (int k = 0; k < K; ++k) Mc += e[k] * c.C[k];
+      if (FF) {
+        const ff2* ef = m.eff_ff + (size_t)(i - m.i_tb0) * K;
+        const ff2* Cf = reinterpret_cast<const ff2*>(c.dk);
+        ff2 acc = {0.0f, 0.0f};
+        for (int k = 0; k < K; ++k) acc = ff_add(acc, ff_mul(ef[k], Cf[k]));
+        Mc = ff_value(acc);
+      } else {
+        for (int k = 0; k < K; ++k) Mc += e[k] * c.C[k];
+      }
       if (i < m.i_fo0) phi = Mc;
     }
     if (i >= m.i_fo0) {
@@ -350,7 +417,7 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
     double w = 0.0, dd = 0.0, at = 0.0;
     for (int e = m.sp_ptr[k]; e < m.sp_ptr[k + 1]; ++e) {
       const int2 en = m.sp_ent[e];
-      const double nu = (double)en.y;
+      const double nu = m.sp_nu[e];
       w += nu * c.q[en.x];
       if (JAC) {
         dd += nu * c.D[en.x];
@@ -402,23 +469,31 @@ __device__ void assemble(const DevMech& m, Cta<NW>& c, const Scal& s, const doub
   for (int k = c.warp; k < K; k += NW) {
     R* row = A + (1 + k) * ld + 1;
     // (1) third-body / falloff part of A_kj = sum_i nu_ki dq_i/dC_j: sum_i nu_ki P_i eff_ij
+    //     (entries outer, columns inner: one multiply-add per element)
     const int t0 = m.tr_ptr[k], t1 = m.tr_ptr[k + 1];
-    for (int j = c.lane; j < K; j += 32) {
-      R a = R(0);
-      for (int t = t0; t < t1; ++t) {
-        const int2 en = m.tr_ent[t];
-        a += R(en.y) * R(c.P[en.x]) * R(m.eff[(size_t)(en.x - m.i_tb0) * K + j]);
+    R acc[8];  // columns lane + 32 u (K <= 256)
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = R(0);
+    for (int t = t0; t < t1; ++t) {
+      const int ri = m.tr_ent[t].x;
+      const R coef = R(m.tr_nu[t] * c.P[ri]);
+      const double* e = m.eff + (size_t)(ri - m.i_tb0) * K;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = c.lane + 32 * u;
+        if (j < K) acc[u] += coef * R(e[j]);
       }
-      row[j] = a;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = c.lane + 32 * u;
+      if (j < K) row[j] = acc[u];
     }
     __syncwarp();
     // (2) mass-action part: one lane per distinct column of the row
     for (int q = m.pr_ptr[k] + c.lane; q < m.pr_ptr[k + 1]; q += 32) {
       R a = R(0);
-      for (int e = m.pr_cptr[q]; e < m.pr_cptr[q + 1]; ++e) {
-        const int2 en = m.pr_ent[e];
-        a += R(en.y) * R(c.dqs[en.x]);
-      }
+      for (int e = m.pr_cptr[q]; e < m.pr_cptr[q + 1]; ++e) a += R(m.pr_nu[e]) * R(c.dqs[m.pr_ent[e].x]);
       row[m.pr_col[q]] += a;
     }
     __syncwarp();
@@ -675,6 +750,155 @@ __device__ int gj_invert(Cta<NW>& c, float* a, int n) {
   return info;
 }
 
+// Gauss-Jordan inverse (FP32) with the matrix held in registers: thread (tr, tc)
+// of a TR x TC grid owns rows tr + TR a (a < RA) and columns tc + TC b (b < CB).
+// Partial pivoting by index (the pivot row is the unused row with the largest
+// |a_ik|, lowest row index on ties; rows are not moved); the normalised pivot row
+// and the multiplier column go through shared memory, and the search for the next
+// pivot is fused into the elimination (two CTA barriers per column). With P the
+// pivot rows in step order and Pinv its inverse, the inverse of the matrix is
+// inv[Pinv[i]][P[j]] = W[i][j]; it is written back to shared memory in that
+// order. Returns 0 or 1 + k for a zero pivot. Requires n <= TR RA and n <= TC CB.
+template <int NW, int TR, int TC, int RA, int CB>
+__device__ int gj_invert_reg(Cta<NW>& c, float* A, int n) {
+  static_assert(TR * TC == NW * 32, "thread grid");
+  static_assert(RA <= 32, "row mask");
+  const int ld = odd_ld(n);
+  const int tr = c.tid / TC, tc = c.tid % TC;
+  unsigned char* pb = reinterpret_cast<unsigned char*>(c.red + SC_PIV);
+  float* pmax = reinterpret_cast<float*>(pb);
+  int* pidx = reinterpret_cast<int*>(pb + 4 * NW);
+  float* pval = reinterpret_cast<float*>(pb + 8 * NW);
+  float* prow = reinterpret_cast<float*>(c.rr);  // n floats
+  float* pcol = prow + n;                        // n floats (rr holds 2 n floats)
+  float w[RA][CB];
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+      const int i = tr + TR * a, j = tc + TC * b;
+      w[a][b] = (i < n && j < n) ? A[i * ld + j] : 0.0f;
+    }
+  unsigned used = 0u;
+  auto publish = [&](float bv, int bi, float bval) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const float ov = __shfl_xor_sync(FULLMASK, bv, o);
+      const int oi = __shfl_xor_sync(FULLMASK, bi, o);
+      const float ox = __shfl_xor_sync(FULLMASK, bval, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; bval = ox; }
+    }
+    if (c.lane == 0) {
+      pmax[c.warp] = bv;
+      pidx[c.warp] = bi;
+      pval[c.warp] = bval;
+    }
+  };
+  {  // candidates for column 0
+    float bv = -1.0f, bval = 0.0f;
+    int bi = n;
+    if (tc == 0) {
+#pragma unroll
+      for (int a = 0; a < RA; ++a) {
+        const int i = tr + TR * a;
+        const float x = fabsf(w[a][0]);
+        if (i < n && (x > bv || (x == bv && i < bi))) { bv = x; bi = i; bval = w[a][0]; }
+      }
+    }
+    publish(bv, bi, bval);
+  }
+  __syncthreads();
+  int info = 0;
+  for (int k = 0; k < n; ++k) {
+    float best = -1.0f, pv = 0.0f;
+    int p = n;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+      const float v = pmax[q];
+      const int i = pidx[q];
+      if (v > best || (v == best && i < p)) { best = v; p = i; pv = pval[q]; }
+    }
+    if (p >= n) {  // no candidate (NaN column): zero pivot on the lowest unused row
+      p = k;
+      pv = 0.0f;
+    }
+    const float pinv = (pv != 0.0f && isfinite(pv)) ? 1.0f / pv : 0.0f;
+    if (pinv == 0.0f && info == 0) info = k + 1;
+    if (c.tid == 0) c.piv[k] = p;
+    const int pa = p / TR, pt = p % TR;
+    const int kb = k / TC, kt = k % TC;
+    if (tr == pt) {
+#pragma unroll
+      for (int a = 0; a < RA; ++a)
+        if (a == pa) {
+#pragma unroll
+          for (int b = 0; b < CB; ++b) {
+            const int j = tc + TC * b;
+            const float v = (j == k ? 1.0f : w[a][b]) * pinv;
+            w[a][b] = v;
+            if (j < n) prow[j] = v;
+          }
+          used |= 1u << a;
+        }
+    }
+    if (tc == kt) {
+#pragma unroll
+      for (int b = 0; b < CB; ++b)
+        if (b == kb) {
+#pragma unroll
+          for (int a = 0; a < RA; ++a) {
+            const int i = tr + TR * a;
+            if (i < n) pcol[i] = w[a][b];
+          }
+        }
+    }
+    __syncthreads();
+    float pr[CB];
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+      const int j = tc + TC * b;
+      pr[b] = j < n ? prow[j] : 0.0f;
+    }
+    const int cn = k + 1, cnb = cn / TC, cnt = cn % TC;
+    float bv = -1.0f, bval = 0.0f;
+    int bi = n;
+#pragma unroll
+    for (int a = 0; a < RA; ++a) {
+      const int i = tr + TR * a;
+      if (i < n && i != p) {
+        const float f = pcol[i];
+#pragma unroll
+        for (int b = 0; b < CB; ++b) {
+          const int j = tc + TC * b;
+          w[a][b] = (j == k ? 0.0f : w[a][b]) - f * pr[b];
+        }
+        if (tc == cnt && !((used >> a) & 1u)) {
+#pragma unroll
+          for (int b = 0; b < CB; ++b)
+            if (b == cnb) {
+              const float x = fabsf(w[a][b]);
+              if (x > bv || (x == bv && i < bi)) { bv = x; bi = i; bval = w[a][b]; }
+            }
+        }
+      }
+    }
+    publish(bv, bi, bval);
+    __syncthreads();
+  }
+  // inverse permutation of the pivot rows, then the scatter into the true inverse
+  for (int k = c.tid; k < n; k += NW * 32) c.perm[c.piv[k]] = k;
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < RA; ++a)
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+      const int i = tr + TR * a, j = tc + TC * b;
+      if (i < n && j < n) A[c.perm[i] * ld + c.piv[j]] = w[a][b];
+    }
+  __syncthreads();
+  return info;
+}
+
 // Solve M x = b for the FP64 right-hand side b; x written as double.
 // FP64: LU forward/back substitution. Otherwise: x = M32^-1 b with the FP32
 // inverse, then `ir` sweeps of r = b - M0 x (FP64, against the assembled matrix
@@ -727,7 +951,15 @@ __device__ int factor(Cta<NW>& c, int n) {
   if constexpr (!Policy<PREC>::IR) {
     return lu_factor<NW, double>(c, reinterpret_cast<double*>(c.M), n);
   } else {
-    return gj_invert<NW>(c, reinterpret_cast<float*>(c.M), n);
+    float* A = reinterpret_cast<float*>(c.M);
+    if constexpr (NW == 4) {
+      if (n <= 64) return gj_invert_reg<4, 8, 16, 8, 4>(c, A, n);
+    } else if constexpr (NW == 8) {
+      if (n <= 128) return gj_invert_reg<8, 16, 16, 8, 8>(c, A, n);
+    } else if constexpr (NW == 2) {
+      if (n <= 64) return gj_invert_reg<2, 4, 16, 16, 4>(c, A, n);
+    }
+    return gj_invert<NW>(c, A, n);
   }
 }
 
@@ -769,7 +1001,7 @@ __device__ double wrms(Cta<NW>& c, int n, const double* e, const double* ya, con
 // Hairer-Wanner starting step (Solving ODEs I, Sec. II.4) in the WRMS norm with
 // scale atol + rtol |y0|, exponent 1/4, clamped to dt; a vanishing derivative
 // selects the whole interval. Uses f0 = f(y0) (already in c.f0) and c.ys, c.fv.
-template <int NW>
+template <int NW, bool FF = false>
 __device__ double starting_step(const DevMech& m, Cta<NW>& c, double p, double dt, double rtol,
                                 double atol) {
   constexpr int NT = NW * 32;
@@ -780,7 +1012,7 @@ __device__ double starting_step(const DevMech& m, Cta<NW>& c, double p, double d
   ha = fmin(ha, dt);
   for (int i = c.tid; i < n; i += NT) c.ys[i] = c.y[i] + ha * c.f0[i];
   __syncthreads();
-  eval_rhs<NW, false>(m, c, c.ys, p, c.fv);
+  eval_rhs<NW, false, FF>(m, c, c.ys, p, c.fv);
   for (int i = c.tid; i < n; i += NT) c.rr[i] = c.fv[i] - c.f0[i];
   __syncthreads();
   const double d2 = wrms(c, n, c.rr, c.y, c.y, rtol, atol) / ha;
@@ -859,8 +1091,8 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
       if (isfinite(g) && g > 0.0) h = fmin(g, dt);
     }
     if (h <= 0.0) {
-      eval_rhs<NW, false>(m, c, c.y, p, c.f0);
-      h = starting_step(m, c, p, dt, rtol, atol);
+      eval_rhs<NW, false, Policy<PREC>::IR>(m, c, c.y, p, c.f0);
+      h = starting_step<NW, Policy<PREC>::IR>(m, c, p, dt, rtol, atol);
     }
     double t = 0.0;
     bool after_reject = false;
@@ -872,7 +1104,7 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
       ++steps;
       // Jacobian and f0 at y; iteration matrix; factorisation
       PHASE(1);
-      const Scal s = eval_rhs<NW, true>(m, c, c.y, p, c.f0);
+      const Scal s = eval_rhs<NW, true, Policy<PREC>::IR>(m, c, c.y, p, c.f0);
       PHASE(2);
       build_matrix<NW, PREC>(m, c, s, c.y, c.f0, 1.0 / (h * kRodasGamma), false);
       PHASE(3);
@@ -895,18 +1127,16 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
             }
             __syncthreads();
             PHASE(4);
-            eval_rhs<NW, false>(m, c, c.ys, p, c.fv);
+            eval_rhs<NW, false, Policy<PREC>::IR>(m, c, c.ys, p, c.fv);
             fs = c.fv;
           }
           PHASE(6);
+          // stage right-hand side f(y_s) + sum_j (c_sj / h) u_j, in place in fv
           for (int i = c.tid; i < n; i += NT) {
             double v = fs[i];
             for (int j = 0; j < st; ++j) v += c_rodasC[st][j] * invh * c.u[j * n + i];
-            c.rr[i] = v;
+            c.fv[i] = v;
           }
-          __syncthreads();
-          // rr is also the IR residual buffer: copy the stage RHS to fv first
-          for (int i = c.tid; i < n; i += NT) c.fv[i] = c.rr[i];
           __syncthreads();
           PHASE(5);
           solve<NW, PREC>(c, n, c.fv, c.u + st * n, args.ir_sweeps);
@@ -972,8 +1202,10 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
+// Four CTAs of 128 threads per SM fit the register file at 128 registers a thread,
+// matching what the shared-memory footprint allows for mechanisms up to ~60 species.
 template <int NW, int PREC>
-__global__ void __launch_bounds__(NW * 32) k_integrate(const __grid_constant__ IntegrateArgs args) {
+__global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : 1) k_integrate(const __grid_constant__ IntegrateArgs args) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long s_work;
   const Layout L = make_layout(args.smem_K, args.smem_I, PREC);
@@ -1024,17 +1256,17 @@ __global__ void __launch_bounds__(NW * 32) k_diag(const __grid_constant__ DiagAr
     __syncthreads();
     const double p = a.p[cell];
     if (a.what == 0) {
-      eval_rhs<NW, false>(a.m, c, c.y, p, c.f0);
+      eval_rhs<NW, false, Policy<PREC>::IR>(a.m, c, c.y, p, c.f0);
       for (int i = c.tid; i < n; i += NT) a.out[(size_t)cell * n + i] = c.f0[i];
     } else if (a.what == 1) {
-      const Scal s = eval_rhs<NW, true>(a.m, c, c.y, p, c.f0);
+      const Scal s = eval_rhs<NW, true, Policy<PREC>::IR>(a.m, c, c.y, p, c.f0);
       build_matrix<NW, PREC>(a.m, c, s, c.y, c.f0, 0.0, true);
       const A* J = reinterpret_cast<const A*>(Policy<PREC>::IR ? c.M0 : c.M);
       for (int i = c.warp; i < n; i += NW)
         for (int j = c.lane; j < n; j += 32) a.out[(size_t)cell * n * n + i * n + j] = (double)J[i * ld + j];
     } else {
-      eval_rhs<NW, false>(a.m, c, c.y, p, c.f0);
-      const double h = starting_step(a.m, c, p, a.dt, a.rtol, a.atol);
+      eval_rhs<NW, false, Policy<PREC>::IR>(a.m, c, c.y, p, c.f0);
+      const double h = starting_step<NW, Policy<PREC>::IR>(a.m, c, p, a.dt, a.rtol, a.atol);
       if (c.tid == 0) a.out[cell] = h;
     }
     __syncthreads();

@@ -65,11 +65,14 @@ def _states(m, n=24, seed=3, p=40e5):
 
 
 # ------------------------------------------------------------------ RHS / Jacobian / h0
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("name", list(_mech_cases().keys()))
-def test_rhs_parity(pkg, orc, name):
+def test_rhs_parity(pkg, orc, name, precision):
+    """RHS vs the oracle; the mixed form (precision 1) evaluates the third-body sums in
+    float-float arithmetic and must stay within the same 1e-11 relative bound."""
     m = _mech_cases()[name]
     st = _states(m)
-    integ = pkg.Integrator(m)
+    integ = pkg.Integrator(m, precision=precision)
     f = integ.eval_rhs(_dev(st.T), _dev(st.p), _dev(st.Y)).cpu().numpy()
     M = orc.Mech(m)
     nu = np.abs(m.net_stoich())
@@ -342,3 +345,16 @@ def test_full_size_c100_mixed_sampled_parity(pkg, orc, ir):
     ref = orc.integrate(m, st.T[pick], st.p[pick], st.Y[pick], dt, RTOL, ATOL)
     _assert_bound(g["T"][pick], g["Y"][pick], ref, f"c100 full size ir={ir}")
     print(f"c100 262k ir={ir}: substeps {g['substeps'].sum()}")
+
+
+def test_autotune_picks_a_block_and_keeps_parity(pkg, orc, tmp_path, monkeypatch):
+    """The autotuner times block sizes on a sample of the call's cells (copies) and
+    keeps the fastest; the caller's cells are integrated once, within the bound, and
+    the choice is cached (in the handle and in the cache file)."""
+    cache = tmp_path / "autotune.txt"
+    monkeypatch.setenv("CHEM_AUTOTUNE_CACHE", str(cache))
+    m, st, dt, ref = _oracle_ref(orc, "c54_65k", 333)
+    g = _run(pkg, m, st, dt, precision=1, autotune=1)
+    _assert_bound(g["T"], g["Y"], ref, "autotune")
+    lines = cache.read_text().split()
+    assert len(lines) == 2 and int(lines[1]) in (64, 128, 256)
