@@ -129,6 +129,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def kernel_traffic(n_cells):
+    """DRAM bytes per launch of the integration kernel from the committed ncu summary
+    (profiles/k_integrate_traffic.txt), scaled from the captured batch to n_cells (state
+    traffic is per cell); None when the kernel source changed since the capture."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "k_integrate_traffic.txt")
+    src = os.path.join(ROOT, "paper_2112_05834_gb300", "csrc", "chem_kernels.cu")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if kv.get("kernel_source_sha256") != digest:
+        return None
+    per_cell = (float(kv["dram_bytes_read"]) + float(kv["dram_bytes_write"])) / float(kv["cells"])
+    return per_cell * n_cells
+
+
 def cpu_baseline(m, st, dt, seconds, seed=0):
     """Oracle on a bounded uniform sample of the workload's cells (all host cores)."""
     import oracle
@@ -291,7 +313,7 @@ def main():
                    "l2": "flushed (256 MB write) before every step", "parallelism": "replicas" if world > 1 else "1 GPU"},
         "plain_fp64": None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": kernel_traffic(n),
                      "note": "FP64 pipe; algorithmic FP64 flops per launch / launch time; peak = nominal GB300 FP64"},
         "clocks": clk,
         "e2e": {"value": world * n * args.steps / e2e_s, "unit": "cells*step/s",

@@ -261,7 +261,7 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
     arr[4 * i + 1] = d->b[o];
     arr[4 * i + 2] = d->Ea_R[o];
     arr[4 * i + 3] = (double)dnu;
-    rev[i] = d->reversible[o] ? 1 : 0;
+    rev[i] = (d->reversible[o] ? 1 : 0) | ((dnu + 1) << 1);
     if (t >= 1) {
       ++n_tb;
       for (int k = 0; k < K; ++k) eff.push_back(d->eff[(size_t)o * K + k]);
@@ -270,7 +270,8 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
       ++n_fo;
       const double* tr4 = d->troe + 4 * o;
       // Troe: reciprocal T*** and T* (Lindemann rows leave them unused)
-      const double f8[8] = {std::log(d->A0[o]), d->b0[o], d->Ea0_R[o], tr4[0],
+      // low-pressure minus high-pressure Arrhenius parameters (k0 / kinf in one exp)
+      const double f8[8] = {std::log(d->A0[o]) - std::log(d->A[o]), d->b0[o] - d->b[o], d->Ea0_R[o] - d->Ea_R[o], tr4[0],
                             t == 3 ? 1.0 / tr4[1] : 0.0, t == 3 ? 1.0 / tr4[2] : 0.0, tr4[3], 0.0};
       fo.insert(fo.end(), f8, f8 + 8);
     }
@@ -306,25 +307,65 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
   std::vector<int2> sp_ent, tr_ent;
   flatten2(sp, sp_ptr, sp_ent);
   flatten2(tr, tr_ptr, tr_ent);
-  // mass-action Jacobian contributions grouped by (row k, column j), fixed order
-  std::vector<int> pr_ptr(K + 1, 0), pr_col, pr_cptr(1, 0);
-  std::vector<int2> pr_ent;
+  // Mass-action Jacobian terms grouped by (row k, column j) pair in a fixed order,
+  // then dealt to the threads of a CTA (longest pair first, to the thread with the
+  // fewest terms so far, lowest thread on ties) for each block size.
+  const int U = (K + 31) / 32, ldm = (K + 1) | 1;
+  std::vector<unsigned> jmask((size_t)K * U, 0u);
+  struct Pair {
+    int k, j;
+    std::vector<int2> ents;  // (4 i + slot, nu_ki)
+  };
+  std::vector<Pair> pairs;
   for (int k = 0; k < K; ++k) {
     std::vector<int4> ents = jr[k];  // (j, i, nu, slot)
     std::stable_sort(ents.begin(), ents.end(), [](const int4& a, const int4& b) { return a.x < b.x; });
     for (size_t e = 0; e < ents.size();) {
-      const int j = ents[e].x;
-      pr_col.push_back(j);
-      for (; e < ents.size() && ents[e].x == j; ++e) pr_ent.push_back(make_int2(4 * ents[e].y + ents[e].w, ents[e].z));
-      pr_cptr.push_back((int)pr_ent.size());
+      Pair pr{k, ents[e].x, {}};
+      for (; e < ents.size() && ents[e].x == pr.j; ++e) pr.ents.push_back(make_int2(4 * ents[e].y + ents[e].w, ents[e].z));
+      jmask[(size_t)k * U + pr.j / 32] |= 1u << (pr.j % 32);
+      pairs.push_back(std::move(pr));
     }
-    pr_ptr[k + 1] = (int)pr_col.size();
+  }
+  std::vector<int> by_len(pairs.size());
+  std::iota(by_len.begin(), by_len.end(), 0);
+  std::stable_sort(by_len.begin(), by_len.end(),
+                   [&](int a, int b) { return pairs[a].ents.size() > pairs[b].ents.size(); });
+  std::vector<int2> js_ent[3];
+  std::vector<double> js_nu[3];
+  int js_rounds[3];
+  for (int v = 0; v < 3; ++v) {
+    const int NT = 64 << v;
+    std::vector<int> load(NT, 0);
+    std::vector<std::vector<int>> own(NT);
+    for (int q : by_len) {
+      int t = 0;
+      for (int u = 1; u < NT; ++u)
+        if (load[u] < load[t]) t = u;
+      own[t].push_back(q);
+      load[t] += (int)pairs[q].ents.size();
+    }
+    const int R = std::max(1, *std::max_element(load.begin(), load.end()));
+    js_rounds[v] = R;
+    js_ent[v].assign((size_t)R * NT, make_int2(-1, -1));
+    js_nu[v].assign((size_t)R * NT, 0.0);
+    for (int t = 0; t < NT; ++t) {
+      int r = 0;
+      for (int q : own[t]) {
+        const Pair& pr = pairs[q];
+        for (size_t e = 0; e < pr.ents.size(); ++e, ++r) {
+          const bool last = e + 1 == pr.ents.size();
+          js_ent[v][(size_t)r * NT + t] = make_int2(pr.ents[e].x, last ? (1 + pr.k) * ldm + 1 + pr.j : -1);
+          js_nu[v][(size_t)r * NT + t] = pr.ents[e].y * d->W[pr.k];
+        }
+      }
+    }
   }
 
-  std::vector<double> sp_nu(sp_ent.size()), pr_nu(pr_ent.size()), tr_nu(tr_ent.size());
+  std::vector<double> sp_nu(sp_ent.size()), tr_nu(tr_ent.size());
   for (size_t e = 0; e < sp_ent.size(); ++e) sp_nu[e] = sp_ent[e].y;
-  for (size_t e = 0; e < pr_ent.size(); ++e) pr_nu[e] = pr_ent[e].y;
-  for (size_t e = 0; e < tr_ent.size(); ++e) tr_nu[e] = tr_ent[e].y;
+  for (int k = 0; k < K; ++k)
+    for (int e = tr_ptr[k]; e < tr_ptr[k + 1]; ++e) tr_nu[e] = tr_ent[e].y * d->W[k];
   std::vector<float> eff_ff(2 * eff.size());
   for (size_t e = 0; e < eff.size(); ++e) {
     const float h = (float)eff[e];
@@ -337,13 +378,16 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
                oS = P.add(slots.data(), slots.size() * sizeof(int4)), oR = P.add(rev.data(), rev.size() * 4),
                oF = P.add(fo.data(), fo.size() * 8), oE = P.add(eff.data(), eff.size() * 8),
                oSp = P.add(sp_ptr.data(), sp_ptr.size() * 4), oSe = P.add(sp_ent.data(), sp_ent.size() * 8),
-               oPp = P.add(pr_ptr.data(), pr_ptr.size() * 4), oPc = P.add(pr_col.data(), pr_col.size() * 4),
-               oPq = P.add(pr_cptr.data(), pr_cptr.size() * 4), oPe = P.add(pr_ent.data(), pr_ent.size() * 8),
                oTp = P.add(tr_ptr.data(), tr_ptr.size() * 4), oTe = P.add(tr_ent.data(), tr_ent.size() * 8),
-               oSn = P.add(sp_nu.data(), sp_nu.size() * 8), oPn = P.add(pr_nu.data(), pr_nu.size() * 8),
-               oTn = P.add(tr_nu.data(), tr_nu.size() * 8),
+               oSn = P.add(sp_nu.data(), sp_nu.size() * 8), oTn = P.add(tr_nu.data(), tr_nu.size() * 8),
+               oJm = P.add(jmask.data(), jmask.size() * 4),
                oCo = P.add(chunk_order.data(), chunk_order.size() * 4),
                oEf = P.add(eff_ff.data(), eff_ff.size() * 4);
+  size_t oJe[3], oJn[3];
+  for (int v = 0; v < 3; ++v) {
+    oJe[v] = P.add(js_ent[v].data(), js_ent[v].size() * sizeof(int2));
+    oJn[v] = P.add(js_nu[v].data(), js_nu[v].size() * 8);
+  }
   CHEM_CUDA(h, cudaMalloc(&h->d_tables, P.host.size()));
   CHEM_CUDA(h, cudaMemcpy(h->d_tables, P.host.data(), P.host.size(), cudaMemcpyHostToDevice));
   unsigned char* b = static_cast<unsigned char*>(h->d_tables);
@@ -367,17 +411,18 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
   m.eff = reinterpret_cast<const double*>(b + oE);
   m.sp_ptr = reinterpret_cast<const int*>(b + oSp);
   m.sp_ent = reinterpret_cast<const int2*>(b + oSe);
-  m.pr_ptr = reinterpret_cast<const int*>(b + oPp);
-  m.pr_col = reinterpret_cast<const int*>(b + oPc);
-  m.pr_cptr = reinterpret_cast<const int*>(b + oPq);
-  m.pr_ent = reinterpret_cast<const int2*>(b + oPe);
   m.tr_ptr = reinterpret_cast<const int*>(b + oTp);
   m.tr_ent = reinterpret_cast<const int2*>(b + oTe);
   m.sp_nu = reinterpret_cast<const double*>(b + oSn);
-  m.pr_nu = reinterpret_cast<const double*>(b + oPn);
   m.tr_nu = reinterpret_cast<const double*>(b + oTn);
   m.chunk_order = reinterpret_cast<const int*>(b + oCo);
   m.eff_ff = reinterpret_cast<const chem::ff2*>(b + oEf);
+  m.jmask = reinterpret_cast<const unsigned*>(b + oJm);
+  for (int v = 0; v < 3; ++v) {
+    m.js_ent[v] = reinterpret_cast<const int2*>(b + oJe[v]);
+    m.js_nu[v] = reinterpret_cast<const double*>(b + oJn[v]);
+    m.js_rounds[v] = js_rounds[v];
+  }
   return CHEM_OK;
 }
 

@@ -45,19 +45,24 @@ struct DevMech {
   const double* arr;    // [I][4]: ln A, b, Ea_R, dnu
   const int4* slots;    // [I]: reactant slot 0/1, product slot 0/1 species (-1 empty);
                         //      a coefficient of 2 appears as two equal slots
-  const int* rev;       // [I] 0/1
-  const double* fo;     // [n_fo][8]: ln A0, b0, Ea0_R, alpha, 1/T***, 1/T*, T**, 0
+  const int* rev;       // [I] bit 0: reversible; bits 1-2: dnu + 1 (dnu = -1, 0, 1)
+  const double* fo;     // [n_fo][8]: ln(A0/A), b0 - b, Ea0_R - Ea_R, alpha, 1/T***, 1/T*, T**, 0
   const double* eff;    // [n_tb][K] (row r belongs to reaction i_tb0 + r)
   const struct ff2* eff_ff;  // the same efficiencies as float-float pairs (hi, lo)
   const int* sp_ptr;    // [K+1] species -> (reaction, nu) CSR
   const int2* sp_ent;
   const double* sp_nu;  // the same nu as doubles
-  const int* pr_ptr;    // [K+1] Jacobian row k -> its distinct mass-action columns q
-  const int* pr_col;    // [npairs] column j (species) of pair q
-  const int* pr_cptr;   // [npairs+1] pair q -> contributions
-  const int2* pr_ent;   // (4 i + slot, nu_ki): nu_ki dq_i/dC(slot) adds to (k, j)
-  const double* pr_nu;  // the same nu as doubles
-  const double* tr_nu;  // nu of the tr_ent entries as doubles
+  // Mass-action Jacobian terms A_kj = sum nu_ki dq_i/dC_j, one sum per (row k,
+  // column j) pair, dealt to the threads of a CTA of 64, 128 or 256 threads
+  // (table v = 0, 1, 2) so that each thread has about as many terms as any other.
+  // Entry (r, t) of table v, at r * (64 << v) + t, is thread t's r-th term:
+  // x = index 4 i + slot into the per-reaction dq/dC data (-1: padding), y = the
+  // matrix offset the finished sum goes to (-1: the pair continues).
+  const int2* js_ent[3];
+  const double* js_nu[3];  // nu_ki W_k of the term
+  int js_rounds[3];
+  const unsigned* jmask;   // [K][ceil(K/32)]: bit l of word (k, u) set if pair (k, l + 32 u) exists
+  const double* tr_nu;  // nu_ki W_k of the tr_ent entries
   const int* tr_ptr;    // [K+1] row k -> (reaction i with [M], nu_ki)
   const int2* tr_ent;
 };

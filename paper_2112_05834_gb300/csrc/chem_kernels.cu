@@ -146,7 +146,9 @@ __host__ __device__ inline Layout make_layout(int Kmax, int Imax, int prec) {
 size_t smem_bytes(int Kmax, int Imax, int prec) { return make_layout(Kmax, Imax, prec).total; }
 
 // Scalars kept in the reduction area (after the 4 x NW partial-sum slots).
-enum { SC_LOGT = 48, SC_INVP = 49, SC_FLAG = 50, SC_MISC = 51, SC_PIV = 52 };  // SC_PIV: 2 x NW slots
+// SC_OUT: 8 broadcast results of Cta::reduce; SC_PIV: pivot search slots (12 NW bytes)
+// (SC_INVT during the rate evaluation, SC_INVP during the LU: never live together)
+enum { SC_OUT = 32, SC_LOGT = 48, SC_INVT = 49, SC_INVP = 49, SC_FLAG = 50, SC_MISC = 51, SC_PIV = 52 };
 
 template <int NW>
 struct Cta {
@@ -205,31 +207,64 @@ struct Cta {
   }
 
   // Sum of NV values over the CTA; every thread receives the same totals
-  // (fixed summation order: deterministic).
+  // (fixed summation order: deterministic). Only the first nw warps may hold
+  // non-zero values (the others skip the shuffle tree). Warp 0 adds the per-warp
+  // partials and passes the totals to fin(tot, out), which derives NO scalars from
+  // them; lane 0's out[] reaches every thread through shared memory, so scalar
+  // follow-up work (reciprocals, roots) runs on one warp instead of all of them.
+  template <int NV, int NO, class F>
+  __device__ void reduce(const double (&v)[NV], int nw, F fin, double (&out)[NO]) {
+    static_assert(NV * NW <= SC_OUT && NO <= 8, "reduction slots");
+    if (warp < nw) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        double x = v[a];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) x += __shfl_down_sync(FULLMASK, x, o);
+        if (lane == 0) red[a * NW + warp] = x;
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double tot[NV];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        double s = red[a * NW];
+        for (int w = 1; w < nw; ++w) s += red[a * NW + w];
+        tot[a] = s;
+      }
+      double o[NO];
+      fin(tot, o);
+      if (lane == 0) {
+#pragma unroll
+        for (int b = 0; b < NO; ++b) red[SC_OUT + b] = o[b];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < NO; ++b) out[b] = red[SC_OUT + b];
+  }
+
+  // Plain CTA sum of NV values (nw as in reduce).
   template <int NV>
-  __device__ void sum(double (&v)[NV]) {
+  __device__ void sum(double (&v)[NV], int nw = NW) {
+    reduce(v, nw, [](const double (&t)[NV], double (&o)[NV]) {
 #pragma unroll
-    for (int a = 0; a < NV; ++a) {
-      double x = v[a];
-#pragma unroll
-      for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULLMASK, x, o);
-      if (lane == 0) red[a * NW + warp] = x;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int a = 0; a < NV; ++a) {
-      double s = 0.0;
-#pragma unroll
-      for (int w = 0; w < NW; ++w) s += red[a * NW + w];
-      v[a] = s;
-    }
-    __syncthreads();
+      for (int a = 0; a < NV; ++a) o[a] = t[a];
+    }, v);
   }
 };
 
+// number of warps that hold data in a loop `for (i = tid; i < count; i += NT)`
+template <int NW>
+__device__ __forceinline__ int warps_for(int count) {
+  const int w = (count + 31) >> 5;
+  return w < NW ? w : NW;
+}
+
 // Cell-level scalars shared by all threads of the CTA (identical in every thread).
 struct Scal {
-  double T, invT, logT, rho, irho, Wbar, cpm, fT, dcpm, Scpw;
+  double T, invT, logT, rho, irho, Wbar, cpm, icpm, fT, dcpm, Scpw;
 };
 
 // ---------------------------------------------------------------------------
@@ -242,23 +277,36 @@ struct Scal {
 template <int NW, bool JAC, bool FF = false>
 __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p, double* f) {
   constexpr int NT = NW * 32;
-  const int K = m.K, I = m.I;
+  const int K = m.K;
   Scal s;
   s.T = y[0];
-  s.invT = 1.0 / s.T;
+  // warp 0: ln T and 1/T for every thread (read after the reduction's barriers)
+  double invT0 = 0.0;
   if (c.warp == 0) {
-    double lg = log(s.T);
-    if (c.lane == 0) c.red[SC_LOGT] = lg;
+    const double lg = log(s.T);
+    invT0 = 1.0 / s.T;
+    if (c.lane == 0) {
+      c.red[SC_LOGT] = lg;
+      c.red[SC_INVT] = invT0;
+    }
   }
   {
     double part[1] = {0.0};
     for (int k = c.tid; k < K; k += NT) part[0] += y[1 + k] * m.invW[k];
-    c.sum(part);
-    s.Wbar = 1.0 / part[0];
-    s.rho = p / (kRc * s.T * part[0]);
-    s.irho = kRc * s.T * part[0] / p;
+    double o[3];
+    const double T = s.T;
+    c.reduce(part, warps_for<NW>(K), [&](const double (&t)[1], double (&r)[3]) {
+      const double Wbar = 1.0 / t[0];
+      r[0] = Wbar;
+      r[1] = p * invT0 * Wbar * (1.0 / kRc);  // rho = p Wbar / (Rc T)
+      r[2] = kRc * T * t[0] / p;              // 1 / rho
+    }, o);
+    s.Wbar = o[0];
+    s.rho = o[1];
+    s.irho = o[2];
   }
   s.logT = c.red[SC_LOGT];
+  s.invT = c.red[SC_INVT];
   const double T = s.T, invT = s.invT, logT = s.logT;
   // species: thermo, exp(G/RT), concentrations
   for (int k = c.tid; k < K; k += NT) {
@@ -309,15 +357,15 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
     const double Pf = Ca * Cb, Pb = Cc * Cd;
     // 1/Kc = exp(dG/RT) (Rc T/P0)^dnu with exp(dG/RT) from the species factors
     double ratio = 0.0;
-    if (m.rev[i]) {
+    const int rv = m.rev[i];
+    if (rv & 1) {
       ratio = c.eg[sl.z] * c.ieg[sl.x];
       if (sl.w >= 0) ratio *= c.eg[sl.w];
       if (sl.y >= 0) ratio *= c.ieg[sl.y];
-      if (ar.w > 0.5) ratio *= cRT;
-      else if (ar.w < -0.5) ratio *= icRT;
+      ratio *= (rv >> 1) == 2 ? cRT : (rv >> 1) == 0 ? icRT : 1.0;
     }
     double Mc = 0.0, phi = 1.0;
-    double dk_dM = 0.0, dlnk = ar.y * invT + ar.z * invT * invT, dk_dT = 0.0;
+    double dk_dM = 0.0, dlnk = (ar.y + ar.z * invT) * invT, dk_dT = 0.0;
     if (i >= m.i_tb0) {
       const double* e = m.eff + (size_t)(i - m.i_tb0) * K;
       if (FF) {
@@ -332,12 +380,12 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
       if (i < m.i_fo0) phi = Mc;
     }
     if (i >= m.i_fo0) {
+      // fo[0..2] hold the low-pressure minus the high-pressure Arrhenius parameters,
+      // so one exponential gives k0 / kinf
       const double* fo = m.fo + 8 * (i - m.i_fo0);
-      const double kinf = kf;
-      const double k0 = exp(fo[0] + fo[1] * logT - fo[2] * invT);
-      const double dlnk0 = fo[1] * invT + fo[2] * invT * invT;
-      const double Pr = k0 * Mc / kinf;
-      double F = 1.0, dF_dPr = 0.0, dF_dT = 0.0;
+      const double r0 = exp(fo[0] + fo[1] * logT - fo[2] * invT);  // k0 / kinf
+      const double Pr = r0 * Mc;
+      double F = 1.0, dlgF_dL = 0.0, dlnF_dT = 0.0;
       if (i >= m.i_troe0) {
         const double alpha = fo[3];
         // fo[4] = 1/T***, fo[5] = 1/T*
@@ -352,29 +400,28 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
         const double lF = log10(Fc);
         const double cc = -0.4 - 0.67 * lF, nn = 0.75 - 1.27 * lF;
         const double x = log10(Pr) + cc;
-        const double den = nn - 0.14 * x;
-        const double f1 = x / den;
-        const double g = 1.0 + f1 * f1;
-        const double lgF = lF / g;
+        const double iden = 1.0 / (nn - 0.14 * x);
+        const double f1 = x * iden;
+        const double ig = 1.0 / (1.0 + f1 * f1);
+        const double lgF = lF * ig;
         F = exp10(lgF);
         if (JAC) {
-          const double ln10 = 2.302585092994046;
-          const double df1_dL = nn / (den * den);
-          const double df1_dlF = (-0.67 * den - x * (-1.27 + 0.14 * 0.67)) / (den * den);
-          const double dlgF_dL = -lF * 2.0 * f1 / (g * g) * df1_dL;
-          const double dlgF_dlF = 1.0 / g - lF * 2.0 * f1 / (g * g) * df1_dlF;
-          dF_dPr = F * dlgF_dL / Pr;
-          dF_dT = F * ln10 * dlgF_dlF * (dFc / (Fc * ln10));
+          // partial derivatives of log10 F by log10 Pr and by log10 Fc
+          const double df1_dL = nn * iden * iden;
+          const double df1_dlF = (-0.67 - f1 * (-1.27 + 0.14 * 0.67)) * iden;
+          dlgF_dL = -2.0 * lgF * ig * f1 * df1_dL;
+          const double dlgF_dlF = ig - 2.0 * lgF * ig * f1 * df1_dlF;
+          dlnF_dT = dlgF_dlF * dFc / Fc;  // d ln F / dT at fixed Pr
         }
       }
       const double red1 = 1.0 / (1.0 + Pr);
+      const double kinf = kf;
       kf = kinf * Pr * red1 * F;
       if (JAC) {
-        const double dPr_dM = k0 / kinf;
-        const double dPr_dT = Pr * (dlnk0 - dlnk);
-        dk_dM = kinf * F * red1 * red1 * dPr_dM + kinf * Pr * red1 * dF_dPr * dPr_dM;
-        dk_dT = kinf * dlnk * Pr * red1 * F + kinf * F * red1 * red1 * dPr_dT +
-                kinf * Pr * red1 * (dF_dT + dF_dPr * dPr_dT);
+        // d ln k / d ln Pr = 1/(1 + Pr) + d log10 F / d log10 Pr; Pr = (k0/kinf) [M]
+        const double g = red1 + dlgF_dL;
+        dk_dM = kinf * red1 * F * g * r0;
+        dk_dT = kf * (dlnk + g * (fo[1] + fo[2] * invT) * invT + dlnF_dT);
       }
     }
     const double kr = kf * ratio;
@@ -394,7 +441,7 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
       double dtc, Pc;
       if (i >= m.i_fo0) {
         const double netc = Pf - ratio * Pb;
-        dtc = dk_dT * netc + (m.rev[i] ? kr * Pb * dlnKc : 0.0);
+        dtc = dk_dT * netc + ((rv & 1) ? kr * Pb * dlnKc : 0.0);
         Pc = dk_dM * netc;
       } else {
         const double dkf = kf * dlnk;
@@ -434,95 +481,155 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
       part[3] += c.cpR[k] * w;                      // sum cp_k omega_k / Rc
     }
   }
-  c.sum(part);
-  s.cpm = kRc * part[1];
-  const double Qh = kRc * T * part[0];
-  s.fT = -Qh / (s.rho * s.cpm);
-  if (JAC) {
-    s.dcpm = kRc * part[2];
-    s.Scpw = kRc * part[3];
+  {
+    double o[5];
+    const double T = s.T, irho = s.irho;
+    c.reduce(part, warps_for<NW>(K), [&](const double (&t)[JAC ? 4 : 2], double (&r)[5]) {
+      const double cpm = kRc * t[1];
+      const double icpm = 1.0 / cpm;
+      const double fT = -kRc * T * t[0] * irho * icpm;  // -Qh / (rho cp), Qh = Rc T sum hRT_k w_k
+      r[0] = cpm;
+      r[1] = icpm;
+      r[2] = fT;
+      if constexpr (JAC) {
+        r[3] = kRc * t[2];
+        r[4] = kRc * t[3];
+      } else {
+        r[3] = r[4] = 0.0;
+      }
+      if (c.lane == 0) f[0] = fT;  // visible after the reduction's last barrier
+    }, o);
+    s.cpm = o[0];
+    s.icpm = o[1];
+    s.fT = o[2];
+    s.dcpm = o[3];
+    s.Scpw = o[4];
   }
-  if (c.tid == 0) f[0] = s.fT;
-  __syncthreads();
   return s;
 }
 
 // ---------------------------------------------------------------------------
-// Jacobian assembly (precision R) from the data of eval_rhs<JAC=true>, one warp per
-// species row: dense third-body/falloff part, sparse mass-action part (per-(row,
-// column) contribution lists, fixed order), rank-one density terms and the
-// temperature column; then the temperature row from column sums. Writes the
-// iteration matrix M = I/(h gamma) - J (fac > 0), or J itself (jac_only).
+// Jacobian assembly (precision R) from the data of eval_rhs<JAC=true>.
+// With A_kj = sum_i nu_ki dq_i/dC_j (mass-action slot terms plus the third-body /
+// falloff term nu_ki P_i eff_ij), the species rows of the Jacobian are
+//   J_kj = (W_k / W_j) (A_kj - (Wbar/rho) d_k) + f_k Wbar / W_j,
+// so with sg = -1 for the iteration matrix M = I/(h gamma) - J (rf = 1/(h gamma))
+// and sg = +1, rf = 0 for the Jacobian itself (JO), the stored value is
+//   S_kj = B_kj / W_j + rf delta_kj,  B_kj = sg W_k A_kj + beta_k,
+//   beta_k = sg (f_k Wbar - W_k (Wbar/rho) d_k).
+// (1) species pass: e_k = h_k / (W_k cp), beta_k, the temperature column
+//     J_k0 = (W_k/rho)(a_kT - d_k/T) + f_k/T; and the mass-action pair sums
+//     sum sg nu_ki W_k dq_i/dC_j on the thread-balanced schedule, stored in place;
+// (2) one warp per row: beta + pair sum, the dense third-body part in registers
+//     (lane l holds columns l + 32 u), scaled by 1/W_j;
+// (3) temperature row from column sums of the stored rows:
+//     J_0j = -sum_k e_k J_kj - f_T cp_j/(W_j cp),
+//     J_00 = -sum_k e_k J_k0 - sum_k cp_k omega_k/(rho cp) - f_T cp'/cp.
 // ---------------------------------------------------------------------------
-template <int NW, class R>
-__device__ void assemble(const DevMech& m, Cta<NW>& c, const Scal& s, const double* y, const double* f,
-                         double fac, bool jac_only, void* target) {
-  constexpr int NT = NW * 32;
-  const int K = m.K, n = K + 1, ld = odd_ld(n);
-  R* A = reinterpret_cast<R*>(target);
-  // stored value S = sg J + fac I  (sg = -1: iteration matrix; sg = +1, fac = 0: Jacobian)
-  const R sg = jac_only ? R(1) : R(-1);
-  const R rf = jac_only ? R(0) : R(fac);
-  // e_k = h_k / (W_k cp) with the molar enthalpy h_k = hRT_k Rc T
-  for (int k = c.tid; k < K; k += NT) c.ek[k] = c.hRT[k] * kRc * s.T * m.invW[k] / s.cpm;
-  const R wr = R(s.Wbar / s.rho), wb = R(s.Wbar);
+template <class R>
+__device__ __forceinline__ R fmaR(R a, R b, R c) {
+  if constexpr (std::is_same<R, float>::value) return fmaf(a, b, c);
+  else return fma(a, b, c);
+}
+
+template <int NW, class R, bool JO, int U>
+__device__ void assemble_rows(const DevMech& m, Cta<NW>& c, R* A, int K, int ld, R rf) {
+  constexpr double SG = JO ? 1.0 : -1.0;
   for (int k = c.warp; k < K; k += NW) {
     R* row = A + (1 + k) * ld + 1;
-    // (1) third-body / falloff part of A_kj = sum_i nu_ki dq_i/dC_j: sum_i nu_ki P_i eff_ij
-    //     (entries outer, columns inner: one multiply-add per element)
-    const int t0 = m.tr_ptr[k], t1 = m.tr_ptr[k + 1];
-    R acc[8];  // columns lane + 32 u (K <= 256)
+    const R beta = R(c.akT[k]);
+    R acc[U];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u] = R(0);
-    for (int t = t0; t < t1; ++t) {
-      const int ri = m.tr_ent[t].x;
-      const R coef = R(m.tr_nu[t] * c.P[ri]);
-      const double* e = m.eff + (size_t)(ri - m.i_tb0) * K;
+    for (int u = 0; u < U; ++u) {
+      const unsigned msk = m.jmask[k * U + u];
+      acc[u] = ((msk >> c.lane) & 1u) ? beta + row[c.lane + 32 * u] : beta;
+    }
+    // third-body / falloff part: 32 row coefficients sg nu_ki W_k P_i at a time,
+    // broadcast from their lanes
+    const int t1 = m.tr_ptr[k + 1];
+    for (int tb = m.tr_ptr[k]; tb < t1; tb += 32) {
+      const int t = tb + c.lane;
+      R cl = R(0);
+      int rl = 0;
+      if (t < t1) {
+        const int ri = m.tr_ent[t].x;
+        cl = R(SG * m.tr_nu[t] * c.P[ri]);
+        rl = ri - m.i_tb0;
+      }
+      const int cnt = min(32, t1 - tb);
+      for (int q = 0; q < cnt; ++q) {
+        const R coef = __shfl_sync(FULLMASK, cl, q);
+        const double* e = m.eff + (size_t)__shfl_sync(FULLMASK, rl, q) * K;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int j = c.lane + 32 * u;
-        if (j < K) acc[u] += coef * R(e[j]);
+        for (int u = 0; u < U; ++u) {
+          const int j = c.lane + 32 * u;
+          if (u < U - 1 || j < K) acc[u] = fmaR(coef, R(e[j]), acc[u]);
+        }
       }
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int j = c.lane + 32 * u;
-      if (j < K) row[j] = acc[u];
+      if (u < U - 1 || j < K) row[j] = fmaR(acc[u], R(m.invW[j]), j == k ? rf : R(0));
     }
-    __syncwarp();
-    // (2) mass-action part: one lane per distinct column of the row
-    for (int q = m.pr_ptr[k] + c.lane; q < m.pr_ptr[k + 1]; q += 32) {
-      R a = R(0);
-      for (int e = m.pr_cptr[q]; e < m.pr_cptr[q + 1]; ++e) a += R(m.pr_nu[e]) * R(c.dqs[m.pr_ent[e].x]);
-      row[m.pr_col[q]] += a;
+  }
+}
+
+template <int NW, class R, bool JO>
+__device__ void assemble(const DevMech& m, Cta<NW>& c, const Scal& s, const double* f, double fac, void* target) {
+  constexpr int NT = NW * 32;
+  constexpr double SG = JO ? 1.0 : -1.0;
+  const int K = m.K, n = K + 1, ld = odd_ld(n);
+  R* A = reinterpret_cast<R*>(target);
+  const R rf = JO ? R(0) : R(fac);
+  // (1) species pass
+  const double eT = kRc * s.T * s.icpm, wr = s.Wbar * s.irho;
+  for (int k = c.tid; k < K; k += NT) {
+    c.ek[k] = c.hRT[k] * eT * m.invW[k];
+    const double Wk = m.W[k], dk = c.dk[k], fk = f[1 + k];
+    A[(1 + k) * ld] = R(SG * (Wk * s.irho * (c.akT[k] - dk * s.invT) + fk * s.invT));
+    c.akT[k] = SG * (fk * s.Wbar - Wk * wr * dk);  // beta_k (a_kT is consumed)
+  }
+  {
+    const int v = NT == 64 ? 0 : NT == 128 ? 1 : 2;
+    const int2* se = m.js_ent[v] + c.tid;
+    const double* sn = m.js_nu[v] + c.tid;
+    const int rounds = m.js_rounds[v];
+    R a = R(0);
+    for (int r = 0; r < rounds; ++r) {
+      const int2 e = se[r * NT];
+      if (e.x >= 0) a = fmaR(R(SG * sn[r * NT]), R(c.dqs[e.x]), a);
+      if (e.y >= 0) {
+        A[e.y] = a;
+        a = R(0);
+      }
     }
-    __syncwarp();
-    // (3) J_kj = (W_k/W_j) (A_kj - (Wbar/rho) d_k) + f_k Wbar / W_j;
-    //     J_k0 = (W_k/rho) (a_kT - d_k / T) + f_k / T
-    const R Wk = R(m.W[k]), dk = R(c.dk[k]), fk = R(f[1 + k]);
-    for (int j = c.lane; j < K; j += 32) {
-      const R iW = R(m.invW[j]);
-      const R J = Wk * iW * (row[j] - wr * dk) + fk * wb * iW;
-      row[j] = sg * J + (j == k ? rf : R(0));
-    }
-    if (c.lane == 0)
-      row[-1] = sg * R(m.W[k] * s.irho * (c.akT[k] - c.dk[k] * s.invT) + f[1 + k] * s.invT);
   }
   __syncthreads();
-  // (4) temperature row: J_0j = -sum_k e_k J_kj - f_T cp_j / (W_j cp);
-  //     J_00 = -sum_k e_k J_k0 - sum_k cp_k omega_k / (rho cp) - f_T cp'/cp,
-  //     with J_kj = sg (S_kj - fac delta) read back from the stored values
+  // (2) species rows
+  switch ((K + 31) >> 5) {
+    case 1: assemble_rows<NW, R, JO, 1>(m, c, A, K, ld, rf); break;
+    case 2: assemble_rows<NW, R, JO, 2>(m, c, A, K, ld, rf); break;
+    case 3: assemble_rows<NW, R, JO, 3>(m, c, A, K, ld, rf); break;
+    case 4: assemble_rows<NW, R, JO, 4>(m, c, A, K, ld, rf); break;
+    case 5: assemble_rows<NW, R, JO, 5>(m, c, A, K, ld, rf); break;
+    case 6: assemble_rows<NW, R, JO, 6>(m, c, A, K, ld, rf); break;
+    case 7: assemble_rows<NW, R, JO, 7>(m, c, A, K, ld, rf); break;
+    default: assemble_rows<NW, R, JO, 8>(m, c, A, K, ld, rf); break;
+  }
+  __syncthreads();
+  // (3) temperature row; with acc = sum_k e_k S_kj, sum_k e_k J_kj = sg (acc - rf e_(j-1)),
+  //     so S_0j = rf e_(j-1) - acc - sg extra_j (j >= 1) and S_00 = rf - acc - sg extra_0
+  const double ft = s.fT * s.icpm;
   for (int j = c.tid; j < n; j += NT) {
     R acc = R(0);
-    for (int k = 0; k < K; ++k) acc += R(c.ek[k]) * A[(1 + k) * ld + j];
-    if (j >= 1) acc -= rf * R(c.ek[j - 1]);
-    acc *= sg;
-    R extra;
+    for (int k = 0; k < K; ++k) acc = fmaR(R(c.ek[k]), A[(1 + k) * ld + j], acc);
+    R v;
     if (j == 0)
-      extra = R(s.Scpw * s.irho / s.cpm + s.fT * s.dcpm / s.cpm);
+      v = rf - acc - R(SG * (s.Scpw * s.irho * s.icpm + ft * s.dcpm));
     else
-      extra = R(s.fT * c.cpR[j - 1] * kRc * m.invW[j - 1] / s.cpm);
-    A[j] = sg * (-acc - extra) + (j == 0 ? rf : R(0));
+      v = rf * R(c.ek[j - 1]) - acc - R(SG * ft * c.cpR[j - 1] * kRc * m.invW[j - 1]);
+    A[j] = v;
   }
   __syncthreads();
 }
@@ -963,17 +1070,16 @@ __device__ int factor(Cta<NW>& c, int n) {
   }
 }
 
-// Assemble the iteration matrix (fac > 0) or the Jacobian (fac == 0, jac_only) in
-// the policy's assembly precision, then give the LU its own copy when they differ.
-template <int NW, int PREC>
-__device__ void build_matrix(const DevMech& m, Cta<NW>& c, const Scal& s, const double* y, const double* f,
-                             double fac, bool jac_only) {
+// Assemble the iteration matrix (fac = 1/(h gamma)) or the Jacobian (JO) in the
+// policy's assembly precision, then give the LU its own copy when they differ.
+template <int NW, int PREC, bool JO>
+__device__ void build_matrix(const DevMech& m, Cta<NW>& c, const Scal& s, const double* f, double fac) {
   using P = Policy<PREC>;
   if constexpr (!P::IR) {
-    assemble<NW, double>(m, c, s, y, f, fac, jac_only, c.M);
+    assemble<NW, double, JO>(m, c, s, f, fac, c.M);
   } else {
-    assemble<NW, typename P::ASM>(m, c, s, y, f, fac, jac_only, c.M0);
-    if (jac_only) return;
+    assemble<NW, typename P::ASM, JO>(m, c, s, f, fac, c.M0);
+    if (JO) return;
     const int n = m.K + 1, ld = odd_ld(n);
     const typename P::ASM* src = reinterpret_cast<const typename P::ASM*>(c.M0);
     float* dst = reinterpret_cast<float*>(c.M);
@@ -983,10 +1089,11 @@ __device__ void build_matrix(const DevMech& m, Cta<NW>& c, const Scal& s, const 
   }
 }
 
-// WRMS norm of e with scale atol + rtol max(|ya|, |yb|).
+// WRMS norm of e with scale atol + rtol max(|ya|, |yb|). With step_fac, also the
+// step-size factor 0.9 err^(-1/4) (kFacMax for err = 0); both come from warp 0.
 template <int NW>
 __device__ double wrms(Cta<NW>& c, int n, const double* e, const double* ya, const double* yb,
-                       double rtol, double atol) {
+                       double rtol, double atol, double* step_fac = nullptr) {
   constexpr int NT = NW * 32;
   double part[1] = {0.0};
   for (int i = c.tid; i < n; i += NT) {
@@ -994,8 +1101,14 @@ __device__ double wrms(Cta<NW>& c, int n, const double* e, const double* ya, con
     const double r = e[i] / sc;
     part[0] += r * r;
   }
-  c.sum(part);
-  return sqrt(part[0] / n);
+  double o[2];
+  c.reduce(part, warps_for<NW>(n), [&](const double (&t)[1], double (&r)[2]) {
+    const double err = sqrt(t[0] / n);
+    r[0] = err;
+    r[1] = err > 0.0 ? kSafety / sqrt(sqrt(err)) : kFacMax;
+  }, o);
+  if (step_fac) *step_fac = o[1];
+  return o[0];
 }
 
 // Hairer-Wanner starting step (Solving ODEs I, Sec. II.4) in the WRMS norm with
@@ -1036,7 +1149,7 @@ __device__ void h_cp_mass(const DevMech& m, Cta<NW>& c, double T, const double* 
     part[0] += Y[k] * hr * m.invW[k];
     part[1] += Y[k] * cpr * m.invW[k];
   }
-  c.sum(part);
+  c.sum(part, warps_for<NW>(m.K));
   h = part[0] * kRc * T;
   cp = part[1] * kRc;
 }
@@ -1076,7 +1189,7 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
   {
     double part[1] = {0.0};
     for (int i = c.tid; i < n; i += NT) part[0] += isfinite(c.y[i]) ? 0.0 : 1.0;
-    c.sum(part);
+    c.sum(part, warps_for<NW>(n));
     if (part[0] > 0.0 || !(c.y[0] > 0.0) || !(p > 0.0)) status = CHEM_CELL_NONFINITE;
   }
   int steps = 0, rejects = 0;
@@ -1106,11 +1219,11 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
       PHASE(1);
       const Scal s = eval_rhs<NW, true, Policy<PREC>::IR>(m, c, c.y, p, c.f0);
       PHASE(2);
-      build_matrix<NW, PREC>(m, c, s, c.y, c.f0, 1.0 / (h * kRodasGamma), false);
+      build_matrix<NW, PREC, false>(m, c, s, c.f0, 1.0 / (h * kRodasGamma));
       PHASE(3);
       const int info = factor<NW, PREC>(c, n);
       PHASE(6);
-      double err;
+      double err, step_fac = kFacMin;
       if (info != 0) {
         err = NAN;
       } else {
@@ -1133,9 +1246,9 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
           PHASE(6);
           // stage right-hand side f(y_s) + sum_j (c_sj / h) u_j, in place in fv
           for (int i = c.tid; i < n; i += NT) {
-            double v = fs[i];
-            for (int j = 0; j < st; ++j) v += c_rodasC[st][j] * invh * c.u[j * n + i];
-            c.fv[i] = v;
+            double v = 0.0;
+            for (int j = 0; j < st; ++j) v += c_rodasC[st][j] * c.u[j * n + i];
+            c.fv[i] = fma(invh, v, fs[i]);
           }
           __syncthreads();
           PHASE(5);
@@ -1149,21 +1262,19 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
           c.yn[i] = v;
         }
         __syncthreads();
-        err = wrms(c, n, c.u + 5 * n, c.y, c.yn, rtol, atol);
+        err = wrms(c, n, c.u + 5 * n, c.y, c.yn, rtol, atol, &step_fac);
       }
       if (!(err <= 1.0)) {
         ++rejects;
         after_reject = true;
-        const double fac = isfinite(err) ? fmax(kSafety * pow(err, -0.25), kFacMin) : kFacMin;
-        h *= fac;
+        h *= isfinite(err) ? fmax(step_fac, kFacMin) : kFacMin;
         continue;
       }
       t += h;
       for (int i = c.tid; i < n; i += NT) c.y[i] = c.yn[i];
       __syncthreads();
       if (h_first == 0.0) h_first = h;
-      double fac = err > 0.0 ? kSafety * pow(err, -0.25) : kFacMax;
-      fac = fmin(fmax(fac, kFacMin), after_reject ? 1.0 : kFacMax);
+      const double fac = fmin(fmax(step_fac, kFacMin), after_reject ? 1.0 : kFacMax);
       after_reject = false;
       h *= fac;
     }
@@ -1260,7 +1371,7 @@ __global__ void __launch_bounds__(NW * 32) k_diag(const __grid_constant__ DiagAr
       for (int i = c.tid; i < n; i += NT) a.out[(size_t)cell * n + i] = c.f0[i];
     } else if (a.what == 1) {
       const Scal s = eval_rhs<NW, true, Policy<PREC>::IR>(a.m, c, c.y, p, c.f0);
-      build_matrix<NW, PREC>(a.m, c, s, c.y, c.f0, 0.0, true);
+      build_matrix<NW, PREC, true>(a.m, c, s, c.f0, 0.0);
       const A* J = reinterpret_cast<const A*>(Policy<PREC>::IR ? c.M0 : c.M);
       for (int i = c.warp; i < n; i += NW)
         for (int j = c.lane; j < n; j += 32) a.out[(size_t)cell * n * n + i * n + j] = (double)J[i * ld + j];
