@@ -274,6 +274,14 @@ chem_status chem_lu_solve_batched(int64_t n_mat, int32_t dim, const double* A, c
                                   void* stream);
 
 /*
+ * y[i] = exp(x[i]) by the exponential the rate kernels use (Tang's table-driven
+ * method; see the kernel source), for n elements of device arrays x, y (n >= 0).
+ * Arguments with |x| >= 672, infinities and NaN follow the CUDA library exp.
+ * Returns CHEM_ERR_INVALID_ARG for n < 0 or NULL arrays with n > 0.
+ */
+chem_status chem_eval_exp(int64_t n, const double* x, double* y, void* stream);
+
+/*
  * The Rosenbrock coefficients the device code uses, in the transformed form
  * (Hairer & Wanner II, Sec. IV.7): gamma, a[6][6], c[6][6] (row-major,
  * strictly lower), m[6] (solution weights), e[6] (error weights). Host only;

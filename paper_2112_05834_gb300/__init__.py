@@ -40,6 +40,7 @@ SIGNATURES = {
     "chem_eval_jacobian": (C.c_int, [_P, _I64, _P, _P, _P, _P, _P]),
     "chem_eval_h0": (C.c_int, [_P, _I64, _P, _P, _P, _D, _D, _D, _P, _P]),
     "chem_lu_solve_batched": (C.c_int, [_I64, _I32, _P, _P, _P, _P, _I32, _I32, _P]),
+    "chem_eval_exp": (C.c_int, [_I64, _P, _P, _P]),
     "chem_rosenbrock_tableau": (None, [_P, _P, _P, _P, _P]),
     "chem_get_phase_cycles": (C.c_int, [_P, _P, _P, _I32]),
     "chem_mlp_create": (C.c_int, [_I32, C.c_uint64, _P]),
@@ -262,6 +263,16 @@ def lu_solve_batched(A, b, precision=0, ir_sweeps=2, stream=None):
                                         _dptr(info), int(precision), int(ir_sweeps),
                                         _stream_ptr(stream)))
     return x, info
+
+
+def eval_exp(x, stream=None):
+    """exp(x) elementwise (CUDA float64 tensor) by the rate kernels' exponential."""
+    import torch
+
+    xc = x.contiguous()
+    y = torch.empty_like(xc)
+    _check(load().chem_eval_exp(xc.numel(), _dptr(xc), _dptr(y), _stream_ptr(stream)))
+    return y
 
 
 def tableau():

@@ -198,21 +198,46 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
   // Each kind group is padded with null reactions to whole 32-reaction chunks, so a
   // warp's chunk never mixes kinds; chunks are dealt to warps by decreasing cost.
   std::vector<int> padded;
-  std::vector<double> chunk_cost;
+  std::vector<double> chunk_cost;  // estimated FP64 instructions of one rate evaluation
   for (int kind = 0; kind < 4; ++kind) {
     size_t first = padded.size();
     for (int i = 0; i < I; ++i)
       if (d->rxn_type[order[i]] == kind) padded.push_back(order[i]);
     if (padded.size() == first) continue;
     while (padded.size() % 32) padded.push_back(-1);
-    const double cost = (kind == 0 ? 1.0 : kind == 1 ? 1.0 : kind == 2 ? 3.0 : 6.0) + (kind ? K / 16.0 : 0.0);
+    const double cost = kind == 0 ? 28.0 : kind == 1 ? 31.0 : kind == 2 ? 60.0 : 220.0;
     for (size_t c = first; c < padded.size(); c += 32) chunk_cost.push_back(cost);
   }
   const int Ip = (int)padded.size();
-  std::vector<int> chunk_order(chunk_cost.size());
-  std::iota(chunk_order.begin(), chunk_order.end(), 0);
-  std::stable_sort(chunk_order.begin(), chunk_order.end(),
-                   [&](int a, int b) { return chunk_cost[a] > chunk_cost[b]; });
+  const int n_chunks = (int)chunk_cost.size();
+  // Deal the chunks to warps, longest first, each to the warp with the least estimated
+  // work so far; the species loops (thermo, production rates: ~72 per 32 species) load
+  // the warps holding species and the CTA's scalar work (~60) the last warp.
+  std::vector<int> by_cost(n_chunks);
+  std::iota(by_cost.begin(), by_cost.end(), 0);
+  std::stable_sort(by_cost.begin(), by_cost.end(), [&](int a, int b) { return chunk_cost[a] > chunk_cost[b]; });
+  std::vector<int> chunk_sched[3];
+  for (int v = 0; v < 3; ++v) {
+    const int NW = 2 << v, NT = 32 * NW;
+    std::vector<double> load(NW, 0.0);
+    for (int w = 0; w < NW; ++w) {
+      int cnt = 0;
+      for (int k = 0; k < K; ++k) cnt += (k % NT) / 32 == w;
+      load[w] = 72.0 * ((cnt + 31) / 32);
+    }
+    load[NW - 1] += 60.0;
+    std::vector<std::vector<int>> own(NW);
+    for (int ch : by_cost) {
+      int w = 0;
+      for (int u = 1; u < NW; ++u)
+        if (load[u] < load[w]) w = u;
+      own[w].push_back(ch);
+      load[w] += chunk_cost[ch];
+    }
+    chunk_sched[v].assign(1, 0);
+    for (int w = 0; w < NW; ++w) chunk_sched[v].push_back(chunk_sched[v].back() + (int)own[w].size());
+    for (int w = 0; w < NW; ++w) chunk_sched[v].insert(chunk_sched[v].end(), own[w].begin(), own[w].end());
+  }
   h->rxn_order = padded;
   std::vector<double> arr((size_t)4 * std::max(Ip, 1), 0.0), fo, eff;
   std::vector<int4> slots(std::max(Ip, 1), make_int4(-1, -1, -1, -1));
@@ -381,10 +406,10 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
                oTp = P.add(tr_ptr.data(), tr_ptr.size() * 4), oTe = P.add(tr_ent.data(), tr_ent.size() * 8),
                oSn = P.add(sp_nu.data(), sp_nu.size() * 8), oTn = P.add(tr_nu.data(), tr_nu.size() * 8),
                oJm = P.add(jmask.data(), jmask.size() * 4),
-               oCo = P.add(chunk_order.data(), chunk_order.size() * 4),
                oEf = P.add(eff_ff.data(), eff_ff.size() * 4);
-  size_t oJe[3], oJn[3];
+  size_t oJe[3], oJn[3], oCs[3];
   for (int v = 0; v < 3; ++v) {
+    oCs[v] = P.add(chunk_sched[v].data(), chunk_sched[v].size() * 4);
     oJe[v] = P.add(js_ent[v].data(), js_ent[v].size() * sizeof(int2));
     oJn[v] = P.add(js_nu[v].data(), js_nu[v].size() * 8);
   }
@@ -394,7 +419,7 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
   DevMech& m = h->dm;
   m.K = K;
   m.I = Ip;
-  m.n_chunks = (int)chunk_order.size();
+  m.n_chunks = n_chunks;
   h->I = std::max(Ip, 1);
   m.n_tb = n_tb;
   m.n_fo = n_fo;
@@ -415,13 +440,13 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
   m.tr_ent = reinterpret_cast<const int2*>(b + oTe);
   m.sp_nu = reinterpret_cast<const double*>(b + oSn);
   m.tr_nu = reinterpret_cast<const double*>(b + oTn);
-  m.chunk_order = reinterpret_cast<const int*>(b + oCo);
   m.eff_ff = reinterpret_cast<const chem::ff2*>(b + oEf);
   m.jmask = reinterpret_cast<const unsigned*>(b + oJm);
   for (int v = 0; v < 3; ++v) {
     m.js_ent[v] = reinterpret_cast<const int2*>(b + oJe[v]);
     m.js_nu[v] = reinterpret_cast<const double*>(b + oJn[v]);
     m.js_rounds[v] = js_rounds[v];
+    m.chunk_sched[v] = reinterpret_cast<const int*>(b + oCs[v]);
   }
   return CHEM_OK;
 }
@@ -847,6 +872,11 @@ extern "C" chem_status chem_lu_solve_batched(int64_t n_mat, int32_t dim, const d
   if (!A || !b || !x) return CHEM_ERR_INVALID_ARG;
   cudaError_t e = launch_lu_solve(n_mat, dim, A, b, x, info, precision, ir_sweeps, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? CHEM_OK : CHEM_ERR_CUDA;
+}
+
+extern "C" chem_status chem_eval_exp(int64_t n, const double* x, double* y, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) return CHEM_ERR_INVALID_ARG;
+  return launch_exp(x, y, n, static_cast<cudaStream_t>(stream)) == cudaSuccess ? CHEM_OK : CHEM_ERR_CUDA;
 }
 
 extern "C" void chem_rosenbrock_tableau(double* gamma, double* a, double* c, double* m, double* e) {

@@ -28,9 +28,11 @@ enum RxnKind { RK_ELEM = 0, RK_TB = 1, RK_LIND = 2, RK_TROE = 3 };
 // Device-resident struct-of-arrays tables of one mechanism. Reactions are stored
 // sorted by kind; species keep the caller's order.
 struct DevMech {
-  int K, I;     // I counts null padding reactions (slot 0 = -1), see chunk_order
+  int K, I;     // I counts null padding reactions (slot 0 = -1): kind groups fill 32-reaction chunks
   int n_chunks;            // I / 32
-  const int* chunk_order;  // [n_chunks] 32-reaction chunks by decreasing cost
+  // Chunks dealt to the warps of a CTA of 64, 128 or 256 threads (table v = 0, 1, 2):
+  // [NW + 1] offsets, then the chunk indices of warp 0, warp 1, ... (NW = 2 << v).
+  const int* chunk_sched[3];
   int n_tb;   // reactions with a third-body concentration (kinds 1..3)
   int n_fo;   // falloff reactions (kinds 2, 3)
   int i_tb0;  // first reaction of kind >= 1 (sorted order)

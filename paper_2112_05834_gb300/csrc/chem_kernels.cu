@@ -64,6 +64,75 @@ __device__ __forceinline__ ff2 ff_mul(ff2 a, ff2 b) {
   return {h, e - (h - p)};
 }
 
+// ---------------------------------------------------------------------------
+// Exponential by Tang's table-driven method (P. T. P. Tang, "Table-driven
+// implementation of the exponential function in IEEE floating-point arithmetic",
+// ACM TOMS 15(2), 1989): x = (32 m + j) ln2/32 + r with |r| <= ln2/64, so
+// exp(x) = 2^m 2^(j/32) exp(r). 2^(j/32) comes from a table of (lead, trail) pairs
+// (lead = 2^(j/32) rounded to double, trail = the remainder rounded to double),
+// exp(r) - 1 from its Taylor polynomial of degree 6 (truncation below 4e-18
+// relative), ln2/32 as a two-term split for the reduction, and 2^m is added to the
+// exponent field. |x| >= 672, infinities and NaN take the library exp. About 11
+// FP64 instructions against ~16 for the library routine on this part.
+// ---------------------------------------------------------------------------
+__device__ const double2 g_exp2_tab[32] = {
+    {1.0, 0.0},
+    {1.0218971486541166, 5.109225028973444e-17},
+    {1.0442737824274138, 8.551889705537965e-17},
+    {1.0671404006768237, -7.899853966841582e-17},
+    {1.0905077326652577, -3.046782079812471e-17},
+    {1.1143867425958924, 1.0410278456845571e-16},
+    {1.1387886347566916, 8.912812676025408e-17},
+    {1.1637248587775775, 3.8292048369240935e-17},
+    {1.189207115002721, 3.982015231465646e-17},
+    {1.215247359980469, -7.712630692681488e-17},
+    {1.241857812073484, 4.658027591836937e-17},
+    {1.2690509571917332, 2.667932131342186e-18},
+    {1.2968395546510096, 2.5382502794888315e-17},
+    {1.3252366431597413, -2.8587312100388614e-17},
+    {1.3542555469368927, 7.70094837980299e-17},
+    {1.383909881963832, -6.770511658794786e-17},
+    {1.4142135623730951, -9.667293313452913e-17},
+    {1.4451808069770467, -3.0237581349939873e-17},
+    {1.4768261459394993, -3.483994556892796e-17},
+    {1.5091644275934228, -1.016455327754295e-16},
+    {1.5422108254079407, 7.949834809697621e-17},
+    {1.5759808451078865, -1.0136916471278304e-17},
+    {1.6104903319492543, 2.4707192569797888e-17},
+    {1.645755478153965, -1.0125679913674773e-16},
+    {1.681792830507429, 8.199010020581497e-17},
+    {1.718619298122478, -1.851380418263111e-17},
+    {1.7562521603732995, 2.960140695448873e-17},
+    {1.7947090750031072, 1.8227458427912087e-17},
+    {1.8340080864093424, 3.283107224245627e-17},
+    {1.8741676341103, -6.122763413004143e-17},
+    {1.9152065613971474, -1.0619946056195963e-16},
+    {1.9571441241754002, 8.960767791036668e-17}
+};
+
+__device__ __noinline__ double exp_outside(double x) { return exp(x); }
+
+__device__ __forceinline__ double xexp(double x, const double2* tab) {
+  if ((__double2hiint(x) & 0x7fffffff) >= 0x40850000) return exp_outside(x);  // |x| >= 672, inf, NaN
+  constexpr double kInvL = 46.16624130844683;      // 32 / ln 2
+  constexpr double kL1 = 0.02166084939249829;      // ln2/32 rounded to double
+  constexpr double kL2 = 7.247021293269686e-19;    // ln2/32 - kL1
+  constexpr double kShift = 6755399441055744.0;    // 1.5 * 2^52: rounds to an integer in the low word
+  const double t = fma(x, kInvL, kShift);
+  const int N = __double2loint(t);
+  const double Nd = t - kShift;
+  double r = fma(-Nd, kL1, x);
+  r = fma(-Nd, kL2, r);
+  double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
+  q = fma(r, q, 1.0 / 24.0);
+  q = fma(r, q, 1.0 / 6.0);
+  q = fma(r, q, 0.5);
+  const double em1 = fma(r * r, q, r);  // exp(r) - 1
+  const double2 sj = tab[N & 31];
+  const double y = sj.x + fma(sj.x, em1, sj.y);
+  return __hiloint2double(__double2hiint(y) + (N >> 5) * (1 << 20), __double2loint(y));
+}
+
 // Rosenbrock coefficients in constant memory (stages are indexed at run time).
 __constant__ double c_rodasA[6][6] = CHEM_RODAS_A;
 __constant__ double c_rodasC[6][6] = CHEM_RODAS_C;
@@ -96,7 +165,7 @@ struct Policy<PREC_FP32ASM> {
 struct Layout {
   int nmax, ld;            // matrix dimension bound and leading dimension (odd)
   int Kmax, Imax;
-  size_t off_vec, off_sp, off_rx, off_M, off_M0, off_piv, off_red, total;
+  size_t off_vec, off_sp, off_rx, off_M, off_M0, off_piv, off_red, off_tab, total;
 };
 
 __host__ __device__ inline int odd_ld(int n) { return n | 1; }
@@ -113,6 +182,8 @@ __host__ __device__ inline Layout make_layout(int Kmax, int Imax, int prec) {
   size_t o = 0;
   L.off_red = o;
   o += 64 * sizeof(double);
+  L.off_tab = o;  // the exponential's table (copied from g_exp2_tab at kernel start)
+  o += 32 * sizeof(double2);
   L.off_vec = o;
   o += (size_t)13 * L.nmax * sizeof(double);
   L.off_sp = o;
@@ -153,6 +224,7 @@ enum { SC_OUT = 32, SC_LOGT = 48, SC_INVT = 49, SC_INVP = 49, SC_FLAG = 50, SC_M
 template <int NW>
 struct Cta {
   static constexpr int NT = NW * 32;
+  static constexpr int SW = NW - 1;  // the warp that finishes reductions and CTA scalars
   int tid, lane, warp;
   double* red;
   // vectors
@@ -165,6 +237,7 @@ struct Cta {
   void* M0;
   int *piv, *perm;
   double* invd;
+  double2* etab;
 
   __device__ void bind(unsigned char* base, const Layout& L) {
     tid = threadIdx.x;
@@ -204,14 +277,21 @@ struct Cta {
     piv = reinterpret_cast<int*>(base + L.off_piv);
     perm = piv + L.nmax;
     invd = reinterpret_cast<double*>(perm + L.nmax);
+    etab = reinterpret_cast<double2*>(base + L.off_tab);
+  }
+
+  // copy the exponential's table to shared memory (visible after the next barrier)
+  __device__ void load_tables() {
+    for (int i = tid; i < 32; i += NT) etab[i] = g_exp2_tab[i];
   }
 
   // Sum of NV values over the CTA; every thread receives the same totals
   // (fixed summation order: deterministic). Only the first nw warps may hold
-  // non-zero values (the others skip the shuffle tree). Warp 0 adds the per-warp
-  // partials and passes the totals to fin(tot, out), which derives NO scalars from
-  // them; lane 0's out[] reaches every thread through shared memory, so scalar
-  // follow-up work (reciprocals, roots) runs on one warp instead of all of them.
+  // non-zero values (the others skip the shuffle tree). The last warp (SW, which
+  // holds no species in the usual case of fewer species than threads) adds the
+  // per-warp partials and passes the totals to fin(tot, out), which derives NO
+  // scalars from them; lane 0's out[] reaches every thread through shared memory,
+  // so scalar follow-up work (reciprocals, roots) runs on one warp, not all.
   template <int NV, int NO, class F>
   __device__ void reduce(const double (&v)[NV], int nw, F fin, double (&out)[NO]) {
     static_assert(NV * NW <= SC_OUT && NO <= 8, "reduction slots");
@@ -225,7 +305,7 @@ struct Cta {
       }
     }
     __syncthreads();
-    if (warp == 0) {
+    if (warp == SW) {
       double tot[NV];
 #pragma unroll
       for (int a = 0; a < NV; ++a) {
@@ -280,9 +360,9 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
   const int K = m.K;
   Scal s;
   s.T = y[0];
-  // warp 0: ln T and 1/T for every thread (read after the reduction's barriers)
+  // the scalar warp: ln T and 1/T for every thread (read after the reduction's barriers)
   double invT0 = 0.0;
-  if (c.warp == 0) {
+  if (c.warp == Cta<NW>::SW) {
     const double lg = log(s.T);
     invT0 = 1.0 / s.T;
     if (c.lane == 0) {
@@ -317,7 +397,7 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
     double sr = a[11] * logT + T * (a[12] + T * (a[13] + T * (a[14] + T * a[15]))) + a[16];
     c.cpR[k] = cp;
     c.hRT[k] = h;
-    const double e = exp(h - sr);
+    const double e = xexp(h - sr, c.etab);
     c.eg[k] = e;
     c.ieg[k] = 1.0 / e;
     const double Ck = s.rho * y[1 + k] * m.invW[k];
@@ -330,12 +410,10 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
   __syncthreads();
   const double cRT = kRc * T / kP0;  // (P0 / (Rc T))^-1
   const double icRT = kP0 * invT / kRc;
-  // 32-reaction chunks of one kind each, dealt to warps in a snake over the
-  // cost-descending chunk order
-  for (int pos = 0; pos < m.n_chunks; ++pos) {
-    const int r = pos % (2 * NW);
-    if ((r < NW ? r : 2 * NW - 1 - r) != c.warp) continue;
-    const int i = m.chunk_order[pos] * 32 + c.lane;
+  // 32-reaction chunks of one kind each, dealt to the warps by estimated work
+  const int* cs = m.chunk_sched[NW == 2 ? 0 : NW == 4 ? 1 : 2];
+  for (int pos = cs[c.warp]; pos < cs[c.warp + 1]; ++pos) {
+    const int i = cs[NW + 1 + pos] * 32 + c.lane;
     const int4 sl = m.slots[i];
     if (sl.x < 0) {  // null padding reaction
       c.q[i] = 0.0;
@@ -349,7 +427,7 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
     const double2 a01 = reinterpret_cast<const double2*>(arp)[0];
     const double2 a23 = reinterpret_cast<const double2*>(arp)[1];
     const struct { double x, y, z, w; } ar = {a01.x, a01.y, a23.x, a23.y};
-    double kf = exp(ar.x + ar.y * logT - ar.z * invT);
+    double kf = xexp(ar.x + ar.y * logT - ar.z * invT, c.etab);
     const double Ca = c.C[sl.x];
     const double Cb = sl.y >= 0 ? c.C[sl.y] : 1.0;
     const double Cc = c.C[sl.z];
@@ -383,17 +461,17 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
       // fo[0..2] hold the low-pressure minus the high-pressure Arrhenius parameters,
       // so one exponential gives k0 / kinf
       const double* fo = m.fo + 8 * (i - m.i_fo0);
-      const double r0 = exp(fo[0] + fo[1] * logT - fo[2] * invT);  // k0 / kinf
+      const double r0 = xexp(fo[0] + fo[1] * logT - fo[2] * invT, c.etab);  // k0 / kinf
       const double Pr = r0 * Mc;
       double F = 1.0, dlgF_dL = 0.0, dlnF_dT = 0.0;
       if (i >= m.i_troe0) {
         const double alpha = fo[3];
         // fo[4] = 1/T***, fo[5] = 1/T*
-        const double e3 = exp(-T * fo[4]), e1 = exp(-T * fo[5]);
+        const double e3 = xexp(-T * fo[4], c.etab), e1 = xexp(-T * fo[5], c.etab);
         double Fc = (1.0 - alpha) * e3 + alpha * e1;
         double dFc = -(1.0 - alpha) * fo[4] * e3 - alpha * fo[5] * e1;
         if (fo[6] > 0.0) {
-          const double e2 = exp(-fo[6] * invT);
+          const double e2 = xexp(-fo[6] * invT, c.etab);
           Fc += e2;
           dFc += fo[6] * invT * invT * e2;
         }
@@ -404,7 +482,7 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
         const double f1 = x * iden;
         const double ig = 1.0 / (1.0 + f1 * f1);
         const double lgF = lF * ig;
-        F = exp10(lgF);
+        F = xexp(lgF * 2.302585092994046, c.etab);  // 10^lgF
         if (JAC) {
           // partial derivatives of log10 F by log10 Pr and by log10 Fc
           const double df1_dL = nn * iden * iden;
@@ -621,7 +699,7 @@ __device__ void assemble(const DevMech& m, Cta<NW>& c, const Scal& s, const doub
   // (3) temperature row; with acc = sum_k e_k S_kj, sum_k e_k J_kj = sg (acc - rf e_(j-1)),
   //     so S_0j = rf e_(j-1) - acc - sg extra_j (j >= 1) and S_00 = rf - acc - sg extra_0
   const double ft = s.fT * s.icpm;
-  for (int j = c.tid; j < n; j += NT) {
+  for (int j = NT - 1 - c.tid; j < n; j += NT) {  // from the last warp down, as the residual rows
     R acc = R(0);
     for (int k = 0; k < K; ++k) acc = fmaR(R(c.ek[k]), A[(1 + k) * ld + j], acc);
     R v;
@@ -1006,6 +1084,126 @@ __device__ int gj_invert_reg(Cta<NW>& c, float* A, int n) {
   return info;
 }
 
+// Gauss-Jordan inverse (FP32) with the matrix in registers, by columns: warp w owns
+// the columns j = w + NW c (c < CC), lane l the rows l + 32 s (s < RS). Partial
+// pivoting by index as in gj_invert_reg (the unused row with the largest |a_ik|,
+// lowest row index on ties; rows are not moved). The warp owning column k searches
+// it, publishes the pivot row p, 1/a_pk and the column (the multipliers) through
+// shared memory (double-buffered), and every warp then broadcasts the pivot row's
+// values of its own columns by warp shuffles and updates them: one CTA barrier per
+// column. Column k is first replaced by the unit vector e_p, so it ends up holding
+// column k of the inverse (in-place Gauss-Jordan). The inverse is written back as
+// inv[Pinv[i]][P[j]] = W[i][j] (P = pivot rows in step order). Requires n <= 32 RS
+// and n <= NW CC. Returns 0 or 1 + k for a zero pivot.
+template <int NW, int RS, int CC>
+__device__ int gj_invert_wc(Cta<NW>& c, float* A, int n) {
+  const int ld = odd_ld(n);
+  const int lane = c.lane, wp = c.warp;
+  float* pcol = reinterpret_cast<float*>(c.u);          // [2][n] multipliers (u: 6 n doubles)
+  int* pp = reinterpret_cast<int*>(c.red + SC_PIV);     // [2] pivot rows
+  float* pinvb = reinterpret_cast<float*>(pp + 2);      // [2] pivot reciprocals
+  float a[RS][CC];
+#pragma unroll
+  for (int s = 0; s < RS; ++s)
+#pragma unroll
+    for (int cc = 0; cc < CC; ++cc) {
+      const int i = lane + 32 * s, j = wp + NW * cc;
+      a[s][cc] = (i < n && j < n) ? A[i * ld + j] : 0.0f;
+    }
+  unsigned used = 0u;  // bit s: row lane + 32 s is a pivot row already
+  // owner warp of column k: search, then publish the pivot and the column
+  auto search = [&](int k, int buf) {
+    const int ck = k / NW;
+    float v[RS];
+#pragma unroll
+    for (int s = 0; s < RS; ++s) v[s] = 0.0f;
+#pragma unroll
+    for (int cc = 0; cc < CC; ++cc)
+      if (cc == ck) {
+#pragma unroll
+        for (int s = 0; s < RS; ++s) v[s] = a[s][cc];
+      }
+    float bv = -1.0f, bval = 0.0f;
+    int bi = n;
+#pragma unroll
+    for (int s = 0; s < RS; ++s) {
+      const int i = lane + 32 * s;
+      const float x = fabsf(v[s]);
+      if (i < n && !((used >> s) & 1u) && (x > bv || (x == bv && i < bi))) { bv = x; bi = i; bval = v[s]; }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const float ov = __shfl_xor_sync(FULLMASK, bv, o);
+      const int oi = __shfl_xor_sync(FULLMASK, bi, o);
+      const float ox = __shfl_xor_sync(FULLMASK, bval, o);
+      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; bval = ox; }
+    }
+#pragma unroll
+    for (int s = 0; s < RS; ++s)
+      if (lane + 32 * s < n) pcol[buf * n + lane + 32 * s] = v[s];
+    if (lane == 0) {
+      const bool ok = bi < n && bval != 0.0f && isfinite(bval);
+      pp[buf] = bi < n ? bi : k;  // no candidate (NaN column): a safe index, zero pivot
+      pinvb[buf] = ok ? 1.0f / bval : 0.0f;
+    }
+  };
+  if (wp == 0) search(0, 0);
+  __syncthreads();
+  int info = 0;
+  for (int k = 0; k < n; ++k) {
+    const int buf = k & 1;
+    const int p = pp[buf];
+    const float pinv = pinvb[buf];
+    if (pinv == 0.0f && info == 0) info = k + 1;
+    if (c.tid == 0) c.piv[k] = p;
+    const int ps = p >> 5, pl = p & 31;
+    float f[RS];
+    bool isp[RS];
+#pragma unroll
+    for (int s = 0; s < RS; ++s) {
+      isp[s] = lane + 32 * s == p;
+      f[s] = lane + 32 * s < n ? pcol[buf * n + lane + 32 * s] : 0.0f;
+    }
+    // column k becomes e_p (it then receives column k of the inverse)
+    if (wp == k % NW) {
+      const int ck = k / NW;
+#pragma unroll
+      for (int cc = 0; cc < CC; ++cc)
+        if (cc == ck) {
+#pragma unroll
+          for (int s = 0; s < RS; ++s) a[s][cc] = isp[s] ? 1.0f : 0.0f;
+        }
+    }
+#pragma unroll
+    for (int cc = 0; cc < CC; ++cc) {
+      float src = a[0][cc];
+#pragma unroll
+      for (int s = 1; s < RS; ++s) src = ps == s ? a[s][cc] : src;
+      const float pr = __shfl_sync(FULLMASK, src, pl) * pinv;  // normalised pivot row
+#pragma unroll
+      for (int s = 0; s < RS; ++s) a[s][cc] = isp[s] ? pr : fmaf(-f[s], pr, a[s][cc]);
+    }
+#pragma unroll
+    for (int s = 0; s < RS; ++s)
+      if (isp[s]) used |= 1u << s;
+    const int k1 = k + 1;
+    if (k1 < n && wp == k1 % NW) search(k1, k1 & 1);
+    __syncthreads();
+  }
+  // inverse permutation of the pivot rows, then the scatter into the true inverse
+  for (int k = c.tid; k < n; k += NW * 32) c.perm[c.piv[k]] = k;
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < RS; ++s)
+#pragma unroll
+    for (int cc = 0; cc < CC; ++cc) {
+      const int i = lane + 32 * s, j = wp + NW * cc;
+      if (i < n && j < n) A[c.perm[i] * ld + c.piv[j]] = a[s][cc];
+    }
+  __syncthreads();
+  return info;
+}
+
 // Solve M x = b for the FP64 right-hand side b; x written as double.
 // FP64: LU forward/back substitution. Otherwise: x = M32^-1 b with the FP32
 // inverse, then `ir` sweeps of r = b - M0 x (FP64, against the assembled matrix
@@ -1017,7 +1215,7 @@ __device__ void solve(Cta<NW>& c, int n, const double* b, double* x, int ir) {
   if constexpr (!P::IR) {
     for (int i = c.tid; i < n; i += NT) x[i] = b[c.perm[i]];
     __syncthreads();
-    if (c.warp == 0) lu_solve_warp<double>(reinterpret_cast<double*>(c.M), n, c.invd, x, c.lane);
+    if (c.warp == Cta<NW>::SW) lu_solve_warp<double>(reinterpret_cast<double*>(c.M), n, c.invd, x, c.lane);
     __syncthreads();
   } else {
     const float* Ai = reinterpret_cast<const float*>(c.M);
@@ -1034,7 +1232,8 @@ __device__ void solve(Cta<NW>& c, int n, const double* b, double* x, int ir) {
     }
     __syncthreads();
     for (int sweep = 0; sweep < ir; ++sweep) {
-      for (int i = c.tid; i < n; i += NT) {
+      // FP64 residual rows from the last warp down (the first warps carry the species loops)
+      for (int i = NT - 1 - c.tid; i < n; i += NT) {
         double acc = b[i];
         const typename P::ASM* row = M0 + i * ld;
         for (int j = 0; j < n; ++j) acc -= (double)row[j] * x[j];
@@ -1060,7 +1259,8 @@ __device__ int factor(Cta<NW>& c, int n) {
   } else {
     float* A = reinterpret_cast<float*>(c.M);
     if constexpr (NW == 4) {
-      if (n <= 64) return gj_invert_reg<4, 8, 16, 8, 4>(c, A, n);
+      if (n <= 56) return gj_invert_wc<4, 2, 14>(c, A, n);
+      if (n <= 64) return gj_invert_wc<4, 2, 16>(c, A, n);
     } else if constexpr (NW == 8) {
       if (n <= 128) return gj_invert_reg<8, 16, 16, 8, 8>(c, A, n);
     } else if constexpr (NW == 2) {
@@ -1322,6 +1522,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : 1) k_integrate(const __
   const Layout L = make_layout(args.smem_K, args.smem_I, PREC);
   Cta<NW> c;
   c.bind(smem, L);
+  c.load_tables();  // first read after the barrier that ends each cell's state load
   for (long long it = 0;; ++it) {
     long long w;
     if (args.sched == SCHED_PLAIN) {
@@ -1359,6 +1560,7 @@ __global__ void __launch_bounds__(NW * 32) k_diag(const __grid_constant__ DiagAr
   const Layout L = make_layout(a.m.K, a.m.I, PREC);
   Cta<NW> c;
   c.bind(smem, L);
+  c.load_tables();
   constexpr int NT = NW * 32;
   const int K = a.m.K, n = K + 1, ld = odd_ld(n);
   for (int64_t cell = blockIdx.x; cell < a.n; cell += gridDim.x) {
@@ -1382,6 +1584,12 @@ __global__ void __launch_bounds__(NW * 32) k_diag(const __grid_constant__ DiagAr
     }
     __syncthreads();
   }
+}
+
+// The rate kernels' exponential, elementwise (diagnostic).
+__global__ void k_exp(const double* x, double* y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = xexp(x[i], g_exp2_tab);
 }
 
 struct LuArgs {
@@ -1502,6 +1710,13 @@ cudaError_t launch_diag(const DevMech& m, int64_t n, const double* T, const doub
   if (prec == PREC_FP64) return launch_simple<PREC_FP64>(k_diag<4, PREC_FP64>, a, smem, grid, st);
   if (prec == PREC_MIXED) return launch_simple<PREC_MIXED>(k_diag<4, PREC_MIXED>, a, smem, grid, st);
   return launch_simple<PREC_FP32ASM>(k_diag<4, PREC_FP32ASM>, a, smem, grid, st);
+}
+
+cudaError_t launch_exp(const double* x, double* y, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = (n + 255) / 256;
+  k_exp<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(x, y, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_lu_solve(int64_t n_mat, int dim, const double* A, const double* b, double* x,
