@@ -202,6 +202,9 @@ chem_status chem_integrate_jobs(const chem_job* jobs, int32_t n_jobs, double dt,
  *   "autotune"    1 = time block sizes on a sample at the first call for a
  *                 new size and keep the fastest
  *   "profile"     1 = accumulate per-phase cycle counters (chem_get_phase_cycles)
+ *   "time_kernel" 1 = record CUDA events on the stream around each integration
+ *                 kernel launch (chem_get_kernel_ms); chem_integrate_noalloc
+ *                 does not record them
  * Errors: CHEM_ERR_INVALID_ARG for an unknown key or out-of-range value.
  */
 chem_status chem_set_option(chem_handle h, const char* key, double value);
@@ -231,6 +234,14 @@ chem_status chem_get_totals(chem_handle h, void* stream, int64_t* n_cells, int64
  * Synchronises `stream`.
  */
 chem_status chem_get_phase_cycles(chem_handle h, void* stream, uint64_t* cycles, int32_t reset);
+
+/*
+ * Device time (ms) of the handle's last integration kernel launch, between CUDA
+ * events recorded on the launching stream just before and after it (with option
+ * "graph", around the graph launch). Waits for that launch to finish. Returns
+ * CHEM_ERR_INVALID_ARG when option "time_kernel" was off for every launch so far.
+ */
+chem_status chem_get_kernel_ms(chem_handle h, float* ms);
 
 /* Last error message of the handle (or of the last chem_create when h is NULL). */
 const char* chem_last_error(chem_handle h);
@@ -274,12 +285,14 @@ chem_status chem_lu_solve_batched(int64_t n_mat, int32_t dim, const double* A, c
                                   void* stream);
 
 /*
- * y[i] = exp(x[i]) by the exponential the rate kernels use (Tang's table-driven
- * method; see the kernel source), for n elements of device arrays x, y (n >= 0).
- * Arguments with |x| >= 672, infinities and NaN follow the CUDA library exp.
- * Returns CHEM_ERR_INVALID_ARG for n < 0 or NULL arrays with n > 0.
+ * y[i] = f(x[i]) for n elements of device arrays x, y (n >= 0) by the elementary
+ * functions the rate kernels use: op 0 exp (Tang's table-driven method), op 1 ln
+ * (table-driven, Tang's manner), op 2 1/x (Newton's iteration on the hardware's
+ * approximate reciprocal); arguments outside their reduced ranges (see the kernel
+ * source) follow the CUDA library routine or the IEEE division. Returns
+ * CHEM_ERR_INVALID_ARG for an unknown op, n < 0 or NULL arrays with n > 0.
  */
-chem_status chem_eval_exp(int64_t n, const double* x, double* y, void* stream);
+chem_status chem_eval_math(int32_t op, int64_t n, const double* x, double* y, void* stream);
 
 /*
  * The Rosenbrock coefficients the device code uses, in the transformed form

@@ -40,7 +40,8 @@ SIGNATURES = {
     "chem_eval_jacobian": (C.c_int, [_P, _I64, _P, _P, _P, _P, _P]),
     "chem_eval_h0": (C.c_int, [_P, _I64, _P, _P, _P, _D, _D, _D, _P, _P]),
     "chem_lu_solve_batched": (C.c_int, [_I64, _I32, _P, _P, _P, _P, _I32, _I32, _P]),
-    "chem_eval_exp": (C.c_int, [_I64, _P, _P, _P]),
+    "chem_eval_math": (C.c_int, [_I32, _I64, _P, _P, _P]),
+    "chem_get_kernel_ms": (C.c_int, [_P, _P]),
     "chem_rosenbrock_tableau": (None, [_P, _P, _P, _P, _P]),
     "chem_get_phase_cycles": (C.c_int, [_P, _P, _P, _I32]),
     "chem_mlp_create": (C.c_int, [_I32, C.c_uint64, _P]),
@@ -213,6 +214,12 @@ class Integrator:
         _check(load().chem_get_phase_cycles(self.h, _stream_ptr(stream), buf, int(bool(reset))), self.h)
         return dict(zip(self.PHASES, (int(v) for v in buf)))
 
+    def kernel_ms(self):
+        """Device time (ms) of the last integration kernel launch (option "time_kernel" = 1)."""
+        ms = C.c_float()
+        _check(load().chem_get_kernel_ms(self.h, C.byref(ms)), self.h)
+        return float(ms.value)
+
     def eval_rhs(self, T, p, Y, stream=None):
         import torch
 
@@ -265,13 +272,15 @@ def lu_solve_batched(A, b, precision=0, ir_sweeps=2, stream=None):
     return x, info
 
 
-def eval_exp(x, stream=None):
-    """exp(x) elementwise (CUDA float64 tensor) by the rate kernels' exponential."""
+def eval_math(op, x, stream=None):
+    """Elementwise exp ("exp"), ln ("log") or 1/x ("rcp") of a CUDA float64 tensor by
+    the rate kernels' own routines."""
     import torch
 
+    code = {"exp": 0, "log": 1, "rcp": 2}[op]
     xc = x.contiguous()
     y = torch.empty_like(xc)
-    _check(load().chem_eval_exp(xc.numel(), _dptr(xc), _dptr(y), _stream_ptr(stream)))
+    _check(load().chem_eval_math(code, xc.numel(), _dptr(xc), _dptr(y), _stream_ptr(stream)))
     return y
 
 

@@ -492,6 +492,8 @@ extern "C" chem_status chem_destroy(chem_handle h) {
   cudaDeviceSynchronize();
   chem_internal_release_learned(h);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->kev0) cudaEventDestroy(h->kev0);
+  if (h->kev1) cudaEventDestroy(h->kev1);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (void* p : h->allocations) cudaFree(p);
   if (h->d_tables) cudaFree(h->d_tables);
@@ -563,6 +565,7 @@ static const OptionDef kOptions[] = {
     {"graph", &chem_handle_s::graph, 0, 1},
     {"autotune", &chem_handle_s::autotune, 0, 1},
     {"profile", &chem_handle_s::profile, 0, 1},
+    {"time_kernel", &chem_handle_s::time_kernel, 0, 1},
 };
 
 extern "C" chem_status chem_set_option(chem_handle h, const char* key, double value) {
@@ -704,9 +707,34 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
 
 // Launch (optionally through a cached CUDA graph).
 chem_status chem_internal_launch(chem_handle h, const IntegrateArgs& a, int block, int grid, cudaStream_t st) {
-  if (h->graph) return chem_internal_graph_launch(h, a, block, grid, st);
-  if (a.sched == SCHED_QUEUE) CHEM_CUDA(h, cudaMemsetAsync(a.queue, 0, sizeof(int), st));
-  CHEM_CUDA(h, launch_integrate(a, block, h->precision, grid, st));
+  if (h->time_kernel && !h->kev0) {
+    CHEM_CUDA(h, cudaEventCreate(&h->kev0));
+    CHEM_CUDA(h, cudaEventCreate(&h->kev1));
+  }
+  if (h->graph) {
+    if (h->time_kernel) CHEM_CUDA(h, cudaEventRecord(h->kev0, st));
+    chem_status s = chem_internal_graph_launch(h, a, block, grid, st);
+    if (s != CHEM_OK) return s;
+  } else {
+    if (a.sched == SCHED_QUEUE) CHEM_CUDA(h, cudaMemsetAsync(a.queue, 0, sizeof(int), st));
+    if (h->time_kernel) CHEM_CUDA(h, cudaEventRecord(h->kev0, st));
+    CHEM_CUDA(h, launch_integrate(a, block, h->precision, grid, st));
+  }
+  if (h->time_kernel) {
+    CHEM_CUDA(h, cudaEventRecord(h->kev1, st));
+    h->kev_recorded = true;
+  }
+  return CHEM_OK;
+}
+
+extern "C" chem_status chem_get_kernel_ms(chem_handle h, float* ms) {
+  if (!h || !ms) return CHEM_ERR_INVALID_ARG;
+  if (!h->kev_recorded) {
+    h->err = "chem_get_kernel_ms: no integration launch was timed (option time_kernel)";
+    return CHEM_ERR_INVALID_ARG;
+  }
+  CHEM_CUDA(h, cudaEventSynchronize(h->kev1));
+  CHEM_CUDA(h, cudaEventElapsedTime(ms, h->kev0, h->kev1));
   return CHEM_OK;
 }
 
@@ -874,9 +902,9 @@ extern "C" chem_status chem_lu_solve_batched(int64_t n_mat, int32_t dim, const d
   return e == cudaSuccess ? CHEM_OK : CHEM_ERR_CUDA;
 }
 
-extern "C" chem_status chem_eval_exp(int64_t n, const double* x, double* y, void* stream) {
-  if (n < 0 || (n > 0 && (!x || !y))) return CHEM_ERR_INVALID_ARG;
-  return launch_exp(x, y, n, static_cast<cudaStream_t>(stream)) == cudaSuccess ? CHEM_OK : CHEM_ERR_CUDA;
+extern "C" chem_status chem_eval_math(int32_t op, int64_t n, const double* x, double* y, void* stream) {
+  if (op < 0 || op > 2 || n < 0 || (n > 0 && (!x || !y))) return CHEM_ERR_INVALID_ARG;
+  return launch_math(op, x, y, n, static_cast<cudaStream_t>(stream)) == cudaSuccess ? CHEM_OK : CHEM_ERR_CUDA;
 }
 
 extern "C" void chem_rosenbrock_tableau(double* gamma, double* a, double* c, double* m, double* e) {

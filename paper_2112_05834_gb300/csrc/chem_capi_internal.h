@@ -35,6 +35,9 @@ struct chem_handle_s {
   int autotune = 0;
   int profile = 0;
   unsigned long long* d_phase = nullptr;  // [8] per-phase cycle counters (option "profile")
+  int time_kernel = 0;                    // option "time_kernel": events around the integration launch
+  cudaEvent_t kev0 = nullptr, kev1 = nullptr;
+  bool kev_recorded = false;
   // per-cell statistics of the last call
   int64_t stats_cap = 0;
   int64_t last_n = 0;

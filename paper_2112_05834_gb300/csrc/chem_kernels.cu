@@ -112,6 +112,8 @@ __device__ const double2 g_exp2_tab[32] = {
 
 __device__ __noinline__ double exp_outside(double x) { return exp(x); }
 
+constexpr double kInvLn10 = 0.43429448190325176;  // 1 / ln 10
+
 __device__ __forceinline__ double xexp(double x, const double2* tab) {
   if ((__double2hiint(x) & 0x7fffffff) >= 0x40850000) return exp_outside(x);  // |x| >= 672, inf, NaN
   constexpr double kInvL = 46.16624130844683;      // 32 / ln 2
@@ -131,6 +133,185 @@ __device__ __forceinline__ double xexp(double x, const double2* tab) {
   const double2 sj = tab[N & 31];
   const double y = sj.x + fma(sj.x, em1, sj.y);
   return __hiloint2double(__double2hiint(y) + (N >> 5) * (1 << 20), __double2loint(y));
+}
+
+// ---------------------------------------------------------------------------
+// Natural logarithm, table-driven in the manner of Tang (P. T. P. Tang, "Table-
+// driven implementation of the logarithm function in IEEE floating-point
+// arithmetic", ACM TOMS 16(4), 1990): x = 2^m y with y in [1, 2), F = 1 + j/128 the
+// nearest of 129 points, c = 1/F rounded to double, r = y c - 1 (one FMA rounding,
+// |r| <= 1/256 + 2^-30), and ln x = m ln 2 - ln c + ln(1 + r), with ln(1 + r) from
+// its Taylor series to degree 7 (truncation below 2e-18 relative). The table holds
+// (c, -ln c as lead + trail) for the rounded c; ln 2 is split so m ln2_hi is exact.
+// Zero, negative, subnormal, infinite and NaN arguments take the library log.
+// ---------------------------------------------------------------------------
+__device__ const double g_log_tab[129][3] = {
+    {1.0, 0.0, 0.0},
+    {0.9922480620155039, 0.007782140442054963, -1.2819179123343749e-20},
+    {0.9846153846153847, 0.015504186535965199, -3.2783210228924137e-19},
+    {0.9770992366412213, 0.023167059281534418, -3.095927552179262e-19},
+    {0.9696969696969697, 0.03077165866675366, 1.0431732029005972e-18},
+    {0.9624060150375939, 0.03831886430213666, -2.3579961573512846e-18},
+    {0.9552238805970149, 0.04580953603129422, 1.6823639049745016e-19},
+    {0.9481481481481482, 0.05324451451881224, 1.803871134979952e-18},
+    {0.9411764705882353, 0.060624621816434854, 2.6424025938726934e-18},
+    {0.9343065693430657, 0.06795066190850778, 3.9239563038692484e-18},
+    {0.927536231884058, 0.07522342123758752, -4.195880720316434e-18},
+    {0.920863309352518, 0.08244366921107454, -4.707903082046854e-18},
+    {0.9142857142857143, 0.08961215868968717, -1.9573659817110993e-18},
+    {0.9078014184397163, 0.09672962645855114, -4.0291867005826106e-18},
+    {0.9014084507042254, 0.10379679368164355, -3.195893222617445e-18},
+    {0.8951048951048951, 0.11081436634029011, 2.0511100808140527e-18},
+    {0.8888888888888888, 0.11778303565638351, -1.1971685747593662e-18},
+    {0.8827586206896552, 0.12470347850095725, -4.6522609636496624e-18},
+    {0.8767123287671232, 0.13157635778871932, 1.112300087972959e-17},
+    {0.8707482993197279, 0.1384023228591192, -1.3766819196398948e-17},
+    {0.8648648648648649, 0.14518200984449783, 8.242418783022477e-18},
+    {0.8590604026845637, 0.151916042025842, 4.1233095848339465e-19},
+    {0.8533333333333334, 0.15860503017663852, 2.583386492298558e-18},
+    {0.847682119205298, 0.16524957289530717, -9.227573884334224e-18},
+    {0.8421052631578947, 0.17185025692665928, -6.022453821011369e-18},
+    {0.8366013071895425, 0.17840765747281825, 1.2720936612962572e-17},
+    {0.8311688311688312, 0.18492233849401193, -7.384679440503435e-18},
+    {0.8258064516129032, 0.19139485299962947, -1.126213516780448e-17},
+    {0.8205128205128205, 0.19782574332991992, -7.995487338741543e-18},
+    {0.8152866242038217, 0.20421554142869083, 7.9379985298027e-18},
+    {0.810126582278481, 0.21056476910734964, 1.136310596906137e-17},
+    {0.8050314465408805, 0.2168739383006143, 6.285749669211092e-18},
+    {0.8, 0.2231435513142097, -9.091270597324798e-18},
+    {0.7950310559006211, 0.2293741010648459, -5.684839459813236e-18},
+    {0.7901234567901234, 0.23556607131276697, -2.394337149518734e-18},
+    {0.7852760736196319, 0.24171993688714513, 1.323779871210866e-17},
+    {0.7804878048780488, 0.2478361639045812, 8.384472133019162e-18},
+    {0.7757575757575758, 0.25391520998096345, -7.180735656435798e-18},
+    {0.7710843373493976, 0.259957524436926, 2.4167516341742964e-17},
+    {0.7664670658682635, 0.2659635484971379, 1.35209848201012e-19},
+    {0.7619047619047619, 0.2719337154836418, 7.833196376974436e-19},
+    {0.757396449704142, 0.2778684510034563, 2.2502748630777633e-17},
+    {0.7529411764705882, 0.2837681731306446, -6.448868003452105e-18},
+    {0.7485380116959064, 0.2896332925830427, 2.0535953219858177e-17},
+    {0.7441860465116279, 0.2954642128938359, -7.768320796245443e-18},
+    {0.7398843930635838, 0.30126133057816185, -1.5120043309967385e-17},
+    {0.735632183908046, 0.3070250352949119, 1.5578716077124932e-18},
+    {0.7314285714285714, 0.3127557100038969, -1.3650721793001109e-17},
+    {0.7272727272727273, 0.3184537311185346, -6.407962483026777e-19},
+    {0.7231638418079096, 0.324119468654212, -4.488767429940198e-18},
+    {0.7191011235955056, 0.32975328637246804, -2.5633554999431966e-17},
+    {0.7150837988826816, 0.3353555419211378, -1.3746739934976202e-17},
+    {0.7111111111111111, 0.3409265869705932, -2.069678002794501e-17},
+    {0.7071823204419889, 0.3464667673462086, -3.591951952851805e-18},
+    {0.7032967032967034, 0.3519764231571781, 2.0005853013367377e-17},
+    {0.6994535519125683, 0.3574558889218038, -2.4269548334425144e-17},
+    {0.6956521739130435, 0.3629054936893685, 6.2632141603179415e-18},
+    {0.6918918918918919, 0.36832556115870757, 2.690672380132659e-17},
+    {0.6881720430107527, 0.373716409793584, -2.449917382477111e-18},
+    {0.6844919786096256, 0.3790783529349695, 1.8481479367349684e-17},
+    {0.6808510638297872, 0.38441169891033206, 8.164631656028572e-18},
+    {0.6772486772486772, 0.38971675114002524, 2.734172667856699e-17},
+    {0.6736842105263158, 0.394993808240869, 7.437680769362324e-18},
+    {0.6701570680628273, 0.40024316412701266, -1.655340963311913e-17},
+    {0.6666666666666666, 0.40546510810816444, -2.881138025962641e-18},
+    {0.6632124352331606, 0.4106599249852683, 2.7752739097728695e-17},
+    {0.6597938144329897, 0.415827895143711, -5.793440801214822e-18},
+    {0.6564102564102564, 0.42096929464412963, 4.5972855136437464e-18},
+    {0.6530612244897959, 0.42608439531090014, -7.056391017993593e-19},
+    {0.649746192893401, 0.43117346481837143, -1.3539234990021841e-17},
+    {0.6464646464646465, 0.43623676677491796, 2.4182887316590065e-17},
+    {0.6432160804020101, 0.4412745608048752, 1.0343758877897315e-17},
+    {0.64, 0.4462871026284195, 1.6511928324886544e-17},
+    {0.6368159203980099, 0.4512746441394586, -9.65179553937242e-18},
+    {0.6336633663366337, 0.4562374334815876, 9.07916350878553e-18},
+    {0.6305418719211823, 0.46117571512217015, 6.140445034134513e-18},
+    {0.6274509803921569, 0.46608972992459924, -2.387354320899491e-19},
+    {0.624390243902439, 0.470979715218791, 7.099457177589995e-18},
+    {0.6213592233009708, 0.475845904869964, 2.5043069845040313e-17},
+    {0.6183574879227053, 0.48068852934575196, -2.7402100563370574e-18},
+    {0.6153846153846154, 0.48550781578170077, -1.6618350693852045e-17},
+    {0.6124401913875598, 0.4903039880451939, 4.612452524535198e-18},
+    {0.6095238095238096, 0.4950772667978514, 1.2508730752094332e-17},
+    {0.6066350710900474, 0.49982786955644926, -2.25665388836583e-18},
+    {0.6037735849056604, 0.5045560107523953, 1.3275397597891851e-17},
+    {0.6009389671361502, 0.5092619017898079, 2.1678544367048826e-17},
+    {0.5981308411214953, 0.5139457511022344, -2.4537074021915265e-18},
+    {0.5953488372093023, 0.5186077642080457, -1.6859591393570242e-17},
+    {0.5925925925925926, 0.5232481437645479, 2.3677269014906905e-17},
+    {0.5898617511520737, 0.5278670896208424, -3.071514383985515e-18},
+    {0.5871559633027523, 0.5324647988694717, 5.4596227307139745e-17},
+    {0.5844748858447488, 0.5370414658968837, -1.9513712761861967e-17},
+    {0.5818181818181818, 0.5415972824327444, 1.108461486609421e-17},
+    {0.579185520361991, 0.5461324375981356, -6.169692458083718e-18},
+    {0.5765765765765766, 0.5506471179526623, -1.3720677478685045e-17},
+    {0.5739910313901345, 0.5551415075405016, -1.449278054403172e-17},
+    {0.5714285714285714, 0.5596157879354228, -2.8656225429134744e-17},
+    {0.5688888888888889, 0.564070138284803, -4.6267923647049475e-17},
+    {0.5663716814159292, 0.5685047353526688, -4.0389558221668317e-17},
+    {0.5638766519823789, 0.5729197535617854, 4.4242614369063874e-17},
+    {0.5614035087719298, 0.5773153650348236, 4.660755938428382e-17},
+    {0.5589519650655022, 0.5816917396346225, 2.7912851075301e-17},
+    {0.5565217391304348, 0.5860490450035782, -4.272669638447342e-17},
+    {0.5541125541125541, 0.5903874466021763, 2.876546074301208e-17},
+    {0.5517241379310345, 0.5947071077466928, 2.7629477772138132e-17},
+    {0.5493562231759657, 0.5990081896460834, 2.5162534548420983e-17},
+    {0.5470085470085471, 0.6032908514380841, 2.0348397202878346e-17},
+    {0.5446808510638298, 0.6075552502245418, -4.1692640626751196e-17},
+    {0.5423728813559322, 0.6118015411059929, -3.392831249677239e-17},
+    {0.540084388185654, 0.616029877215514, 4.9247969628553695e-17},
+    {0.5378151260504201, 0.6202404097518576, 3.4764762563436685e-18},
+    {0.5355648535564853, 0.6244332880118936, 1.4444646832738594e-17},
+    {0.5333333333333333, 0.6286086594223742, -5.360577204673081e-17},
+    {0.5311203319502075, 0.6327666695710378, 5.223564575344447e-17},
+    {0.5289256198347108, 0.6369074622370692, 2.6473983119023558e-17},
+    {0.5267489711934157, 0.6410311794209312, -3.4765774267087093e-17},
+    {0.5245901639344263, 0.6451379613735847, -5.110700818729212e-17},
+    {0.5224489795918368, 0.6492279466251097, -1.3266356651077771e-17},
+    {0.5203252032520326, 0.6533012720127456, -3.7864752792363655e-17},
+    {0.5182186234817814, 0.65735807270836, 2.2462005860533567e-17},
+    {0.5161290322580645, 0.661398482245365, 2.015224182999491e-17},
+    {0.5140562248995983, 0.6654226325450905, 5.424612435933966e-17},
+    {0.512, 0.6694306539426292, 7.420657727561746e-18},
+    {0.5099601593625498, 0.6734226752121667, 3.84128539325942e-17},
+    {0.5079365079365079, 0.6773988235918061, 5.341333284299263e-17},
+    {0.5059288537549407, 0.6813592248079031, 1.7765482243852914e-17},
+    {0.5039370078740157, 0.6853040030989195, -4.8209665191998585e-17},
+    {0.5019607843137255, 0.689233281238809, -9.330006029414747e-18},
+    {0.5, 0.6931471805599453, 2.3190468138462996e-17}
+};
+
+__device__ __noinline__ double log_outside(double x) { return log(x); }
+
+__device__ __forceinline__ double xlog(double x) {
+  const int hx = __double2hiint(x);
+  if (hx < 0x00100000 || hx >= 0x7ff00000) return log_outside(x);
+  constexpr double kLn2Hi = 0.6931467056274414;      // ln 2 with the low 32 mantissa bits cleared
+  constexpr double kLn2Lo = 4.7493250390316726e-07;  // ln 2 - kLn2Hi
+  const int mb = hx & 0x000fffff;
+  const int j = (mb + 0x1000) >> 13;
+  const double y = __hiloint2double(mb | 0x3ff00000, __double2loint(x));
+  const double* e = g_log_tab[j];
+  const double r = fma(y, __ldg(e), -1.0);
+  double q = fma(r, 1.0 / 7.0, -1.0 / 6.0);
+  q = fma(r, q, 1.0 / 5.0);
+  q = fma(r, q, -0.25);
+  q = fma(r, q, 1.0 / 3.0);
+  q = fma(r, q, -0.5);
+  const double l1p = fma(r * r, q, r);  // ln(1 + r)
+  const double md = (double)((hx >> 20) - 1023);
+  const double t = fma(md, kLn2Hi, __ldg(e + 1));
+  return t + fma(md, kLn2Lo, __ldg(e + 2) + l1p);
+}
+
+// 1/x by Newton's iteration r <- r + r (1 - x r) from the hardware's approximate
+// reciprocal (two steps take its error below one ulp); magnitudes outside
+// [2^-1000, 2^1000], zero, infinities and NaN take the IEEE division.
+__device__ __forceinline__ double xrcp(double x) {
+  const int ex = (__double2hiint(x) >> 20) & 0x7ff;
+  if (ex < 23 || ex > 2023) return 1.0 / x;
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
 }
 
 // Rosenbrock coefficients in constant memory (stages are indexed at run time).
@@ -363,8 +544,8 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
   // the scalar warp: ln T and 1/T for every thread (read after the reduction's barriers)
   double invT0 = 0.0;
   if (c.warp == Cta<NW>::SW) {
-    const double lg = log(s.T);
-    invT0 = 1.0 / s.T;
+    const double lg = xlog(s.T);
+    invT0 = xrcp(s.T);
     if (c.lane == 0) {
       c.red[SC_LOGT] = lg;
       c.red[SC_INVT] = invT0;
@@ -376,7 +557,7 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
     double o[3];
     const double T = s.T;
     c.reduce(part, warps_for<NW>(K), [&](const double (&t)[1], double (&r)[3]) {
-      const double Wbar = 1.0 / t[0];
+      const double Wbar = xrcp(t[0]);
       r[0] = Wbar;
       r[1] = p * invT0 * Wbar * (1.0 / kRc);  // rho = p Wbar / (Rc T)
       r[2] = kRc * T * t[0] / p;              // 1 / rho
@@ -399,7 +580,7 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
     c.hRT[k] = h;
     const double e = xexp(h - sr, c.etab);
     c.eg[k] = e;
-    c.ieg[k] = 1.0 / e;
+    c.ieg[k] = xrcp(e);
     const double Ck = s.rho * y[1 + k] * m.invW[k];
     c.C[k] = Ck;
     // float-float copy of C for the third-body sums (the slot of d_k, which the
@@ -475,12 +656,12 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
           Fc += e2;
           dFc += fo[6] * invT * invT * e2;
         }
-        const double lF = log10(Fc);
+        const double lF = xlog(Fc) * kInvLn10;
         const double cc = -0.4 - 0.67 * lF, nn = 0.75 - 1.27 * lF;
-        const double x = log10(Pr) + cc;
-        const double iden = 1.0 / (nn - 0.14 * x);
+        const double x = xlog(Pr) * kInvLn10 + cc;
+        const double iden = xrcp(nn - 0.14 * x);
         const double f1 = x * iden;
-        const double ig = 1.0 / (1.0 + f1 * f1);
+        const double ig = xrcp(fma(f1, f1, 1.0));
         const double lgF = lF * ig;
         F = xexp(lgF * 2.302585092994046, c.etab);  // 10^lgF
         if (JAC) {
@@ -489,10 +670,10 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
           const double df1_dlF = (-0.67 - f1 * (-1.27 + 0.14 * 0.67)) * iden;
           dlgF_dL = -2.0 * lgF * ig * f1 * df1_dL;
           const double dlgF_dlF = ig - 2.0 * lgF * ig * f1 * df1_dlF;
-          dlnF_dT = dlgF_dlF * dFc / Fc;  // d ln F / dT at fixed Pr
+          dlnF_dT = dlgF_dlF * dFc * xrcp(Fc);  // d ln F / dT at fixed Pr
         }
       }
-      const double red1 = 1.0 / (1.0 + Pr);
+      const double red1 = xrcp(1.0 + Pr);
       const double kinf = kf;
       kf = kinf * Pr * red1 * F;
       if (JAC) {
@@ -564,7 +745,7 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
     const double T = s.T, irho = s.irho;
     c.reduce(part, warps_for<NW>(K), [&](const double (&t)[JAC ? 4 : 2], double (&r)[5]) {
       const double cpm = kRc * t[1];
-      const double icpm = 1.0 / cpm;
+      const double icpm = xrcp(cpm);
       const double fT = -kRc * T * t[0] * irho * icpm;  // -Qh / (rho cp), Qh = Rc T sum hRT_k w_k
       r[0] = cpm;
       r[1] = icpm;
@@ -1586,10 +1767,10 @@ __global__ void __launch_bounds__(NW * 32) k_diag(const __grid_constant__ DiagAr
   }
 }
 
-// The rate kernels' exponential, elementwise (diagnostic).
-__global__ void k_exp(const double* x, double* y, int64_t n) {
+// The rate kernels' elementary functions, elementwise (diagnostic): op 0 exp, 1 log, 2 1/x.
+__global__ void k_math(int op, const double* x, double* y, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = xexp(x[i], g_exp2_tab);
+    y[i] = op == 0 ? xexp(x[i], g_exp2_tab) : op == 1 ? xlog(x[i]) : xrcp(x[i]);
 }
 
 struct LuArgs {
@@ -1712,10 +1893,10 @@ cudaError_t launch_diag(const DevMech& m, int64_t n, const double* T, const doub
   return launch_simple<PREC_FP32ASM>(k_diag<4, PREC_FP32ASM>, a, smem, grid, st);
 }
 
-cudaError_t launch_exp(const double* x, double* y, int64_t n, cudaStream_t st) {
+cudaError_t launch_math(int op, const double* x, double* y, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int64_t blocks = (n + 255) / 256;
-  k_exp<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(x, y, n);
+  k_math<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(op, x, y, n);
   return cudaGetLastError();
 }
 

@@ -114,7 +114,12 @@ def test_starting_step_parity(pkg, orc):
         np.testing.assert_allclose(h[c], orc.h0(M, st.p[c], y, 1e-6, RTOL, ATOL), rtol=1e-10)
 
 
-# ------------------------------------------------------------------ exponential
+# ------------------------------------------------------------------ elementary functions
+def _ulp_err(y, x, fn):
+    ref = fn(x.astype(np.longdouble))
+    return np.abs((y.astype(np.longdouble) - ref) / ref).astype(np.float64)
+
+
 def test_exp_accuracy(pkg):
     """The rate kernels' table-driven exponential against exp in extended precision:
     within 1 ulp over the table/polynomial range, the library's behaviour outside it."""
@@ -123,17 +128,53 @@ def test_exp_accuracy(pkg):
                         rng.uniform(-0.02, 0.02, 20000),
                         np.arange(-2000, 2001) * (np.log(2.0) / 32.0),  # table nodes
                         [0.0, -0.0, 1e-300, -1e-300, 671.9, -671.9]])
-    y = pkg.eval_exp(_dev(x)).cpu().numpy()
-    ref = np.exp(x.astype(np.longdouble))
-    rel = np.abs((y.astype(np.longdouble) - ref) / ref).astype(np.float64)
-    print("max relative error:", rel.max())
+    y = pkg.eval_math("exp", _dev(x)).cpu().numpy()
+    rel = _ulp_err(y, x, np.exp)
+    print("exp: max relative error", rel.max())
     assert rel.max() <= 2.3e-16
     assert np.all(y[x == 0.0] == 1.0)
     # outside the reduced range: the library exponential (overflow, underflow, inf, NaN)
     xo = np.array([672.0, 700.0, 709.7, -700.0, 710.0, -800.0, np.inf, -np.inf, np.nan])
-    yo = pkg.eval_exp(_dev(xo)).cpu().numpy()
+    yo = pkg.eval_math("exp", _dev(xo)).cpu().numpy()
     np.testing.assert_allclose(yo[:4], np.exp(xo[:4]), rtol=4e-16)
     assert yo[4] == np.inf and yo[5] == 0.0 and yo[6] == np.inf and yo[7] == 0.0 and np.isnan(yo[8])
+
+
+def test_log_accuracy(pkg):
+    """Table-driven logarithm: absolute error within 1 ulp of ln x plus a few ulp of
+    the result over the arguments the rate kernels meet (T, F_cent, P_r) and across
+    binades; the library's behaviour for zero, negative, subnormal, inf and NaN."""
+    rng = np.random.default_rng(12)
+    x = np.concatenate([rng.uniform(200.0, 6000.0, 200000), 10.0 ** rng.uniform(-300, 300, 200000),
+                        rng.uniform(0.5, 2.0, 100000), 1.0 + np.arange(-64, 129) / 128.0,
+                        [1.0, 2.0, 0.5, 1.0 + 2.0 ** -40, 1.0 - 2.0 ** -40, 2.2250738585072014e-308]])
+    y = pkg.eval_math("log", _dev(x)).cpu().numpy()
+    ref = np.log(x.astype(np.longdouble))
+    err = np.abs(y.astype(np.longdouble) - ref).astype(np.float64)
+    bound = 2.3e-16 * np.abs(ref.astype(np.float64)) + 2.3e-19
+    print("log: max error / bound", (err / bound).max())
+    assert np.all(err <= bound)
+    assert y[x == 1.0][0] == 0.0
+    xo = np.array([0.0, -1.0, 1e-310, np.inf, np.nan])
+    yo = pkg.eval_math("log", _dev(xo)).cpu().numpy()
+    assert yo[0] == -np.inf and np.isnan(yo[1]) and yo[3] == np.inf and np.isnan(yo[4])
+    np.testing.assert_allclose(yo[2], np.log(1e-310), rtol=1e-15)
+
+
+def test_rcp_accuracy(pkg):
+    """Newton reciprocal: within 1 ulp of 1/x; IEEE division outside its range."""
+    rng = np.random.default_rng(13)
+    x = np.concatenate([10.0 ** rng.uniform(-290, 290, 200000) * rng.choice([-1.0, 1.0], 200000),
+                        rng.uniform(1.0, 2.0, 100000), [1.0, -1.0, 3.0, 0.1]])
+    y = pkg.eval_math("rcp", _dev(x)).cpu().numpy()
+    rel = _ulp_err(y, x, lambda v: 1 / v)
+    print("rcp: max relative error", rel.max())
+    assert rel.max() <= 2.3e-16
+    assert y[x == 1.0][0] == 1.0
+    xo = np.array([0.0, -0.0, np.inf, np.nan, 1e-305, 1e305])
+    yo = pkg.eval_math("rcp", _dev(xo)).cpu().numpy()
+    assert yo[0] == np.inf and yo[1] == -np.inf and yo[2] == 0.0 and np.isnan(yo[3])
+    np.testing.assert_allclose(yo[4:], 1 / xo[4:], rtol=2.3e-16)
 
 
 # ------------------------------------------------------------------ LU
