@@ -195,7 +195,8 @@ chem_status chem_integrate_jobs(const chem_job* jobs, int32_t n_jobs, double dt,
  *                 model, see chem_mlp_*); 2 = last-call cost order
  *   "h0"          0 = starting-step heuristic; 1 = learned initial step
  *   "max_steps"   step budget per cell (default 100000)
- *   "block"       threads per cell: 64, 128 or 256 (default 128)
+ *   "block"       threads per cell: 64, 128 or 256; 0 (default) = the size with
+ *                 the most resident warps per SM for the mechanism and precision
  *   "ctas_per_sm" resident CTAs per SM for persistent schedulers (0 = maximum)
  *   "graph"       1 = capture the launch sequence in a CUDA graph and replay it
  *                 while arguments repeat

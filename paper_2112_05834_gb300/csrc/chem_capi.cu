@@ -560,7 +560,7 @@ static const OptionDef kOptions[] = {
     {"order", &chem_handle_s::order, 0, 2},
     {"h0", &chem_handle_s::h0mode, 0, 1},
     {"max_steps", &chem_handle_s::max_steps, 1, 2147483647.0},
-    {"block", &chem_handle_s::block, 64, 256},
+    {"block", &chem_handle_s::block, 0, 256},
     {"ctas_per_sm", &chem_handle_s::ctas_per_sm, 0, 64},
     {"graph", &chem_handle_s::graph, 0, 1},
     {"autotune", &chem_handle_s::autotune, 0, 1},
@@ -576,8 +576,8 @@ extern "C" chem_status chem_set_option(chem_handle h, const char* key, double va
       h->err = std::string("chem_set_option: value out of range for ") + key;
       return CHEM_ERR_INVALID_ARG;
     }
-    if (std::strcmp(key, "block") == 0 && value != 64 && value != 128 && value != 256) {
-      h->err = "chem_set_option: block must be 64, 128 or 256";
+    if (std::strcmp(key, "block") == 0 && value != 0 && value != 64 && value != 128 && value != 256) {
+      h->err = "chem_set_option: block must be 0 (automatic), 64, 128 or 256";
       return CHEM_ERR_INVALID_ARG;
     }
     h->*(o.field) = (int)value;
@@ -678,7 +678,7 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
     h0->err = "chem_integrate: mechanism too large for shared memory";
     return CHEM_ERR_INVALID_ARG;
   }
-  int block = h0->block;
+  int block = h0->block ? h0->block : chem_internal_pick_block(h0, a.smem_K, a.smem_I);
   if (h0->autotune) {
     s = chem_internal_autotune(h0, a, st, &block);
     if (s != CHEM_OK) return s;
@@ -703,6 +703,24 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
     jobs[j].h->cost_n = jobs[j].n_cells;
   }
   return CHEM_OK;
+}
+
+// Block size with the most resident warps per SM for this mechanism size and
+// precision (ties: 128, then 64, then 256 threads).
+int chem_internal_pick_block(chem_handle h, int K, int I) {
+  int best = 128, best_w = -1;
+  for (int b : {128, 64, 256}) {
+    int occ = 0;
+    if (occupancy_integrate(b, h->precision, K, I, &occ) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (occ * b / 32 > best_w) {
+      best_w = occ * b / 32;
+      best = b;
+    }
+  }
+  return best;
 }
 
 // Launch (optionally through a cached CUDA graph).

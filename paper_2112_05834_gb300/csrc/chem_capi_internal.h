@@ -29,7 +29,7 @@ struct chem_handle_s {
   int order = 0;
   int h0mode = 0;
   int max_steps = 100000;
-  int block = 128;
+  int block = 0;  // 0: chosen per call by chem_internal_pick_block
   int ctas_per_sm = 0;
   int graph = 0;
   int autotune = 0;
@@ -73,6 +73,7 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
                                     cudaStream_t st);
 chem_status chem_internal_launch(chem_handle h, const chem::IntegrateArgs& a, int block, int grid,
                                  cudaStream_t st);
+int chem_internal_pick_block(chem_handle h, int K, int I);
 chem_status chem_internal_graph_launch(chem_handle h, const chem::IntegrateArgs& a, int block, int grid,
                                        cudaStream_t st);
 chem_status chem_internal_autotune(chem_handle h, const chem::IntegrateArgs& a, cudaStream_t st, int* block);

@@ -1116,160 +1116,11 @@ __device__ int gj_invert(Cta<NW>& c, float* a, int n) {
   return info;
 }
 
-// Gauss-Jordan inverse (FP32) with the matrix held in registers: thread (tr, tc)
-// of a TR x TC grid owns rows tr + TR a (a < RA) and columns tc + TC b (b < CB).
-// Partial pivoting by index (the pivot row is the unused row with the largest
-// |a_ik|, lowest row index on ties; rows are not moved); the normalised pivot row
-// and the multiplier column go through shared memory, and the search for the next
-// pivot is fused into the elimination (two CTA barriers per column). With P the
-// pivot rows in step order and Pinv its inverse, the inverse of the matrix is
-// inv[Pinv[i]][P[j]] = W[i][j]; it is written back to shared memory in that
-// order. Returns 0 or 1 + k for a zero pivot. Requires n <= TR RA and n <= TC CB.
-template <int NW, int TR, int TC, int RA, int CB>
-__device__ int gj_invert_reg(Cta<NW>& c, float* A, int n) {
-  static_assert(TR * TC == NW * 32, "thread grid");
-  static_assert(RA <= 32, "row mask");
-  const int ld = odd_ld(n);
-  const int tr = c.tid / TC, tc = c.tid % TC;
-  unsigned char* pb = reinterpret_cast<unsigned char*>(c.red + SC_PIV);
-  float* pmax = reinterpret_cast<float*>(pb);
-  int* pidx = reinterpret_cast<int*>(pb + 4 * NW);
-  float* pval = reinterpret_cast<float*>(pb + 8 * NW);
-  float* prow = reinterpret_cast<float*>(c.rr);  // n floats
-  float* pcol = prow + n;                        // n floats (rr holds 2 n floats)
-  float w[RA][CB];
-#pragma unroll
-  for (int a = 0; a < RA; ++a)
-#pragma unroll
-    for (int b = 0; b < CB; ++b) {
-      const int i = tr + TR * a, j = tc + TC * b;
-      w[a][b] = (i < n && j < n) ? A[i * ld + j] : 0.0f;
-    }
-  unsigned used = 0u;
-  auto publish = [&](float bv, int bi, float bval) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      const float ov = __shfl_xor_sync(FULLMASK, bv, o);
-      const int oi = __shfl_xor_sync(FULLMASK, bi, o);
-      const float ox = __shfl_xor_sync(FULLMASK, bval, o);
-      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; bval = ox; }
-    }
-    if (c.lane == 0) {
-      pmax[c.warp] = bv;
-      pidx[c.warp] = bi;
-      pval[c.warp] = bval;
-    }
-  };
-  {  // candidates for column 0
-    float bv = -1.0f, bval = 0.0f;
-    int bi = n;
-    if (tc == 0) {
-#pragma unroll
-      for (int a = 0; a < RA; ++a) {
-        const int i = tr + TR * a;
-        const float x = fabsf(w[a][0]);
-        if (i < n && (x > bv || (x == bv && i < bi))) { bv = x; bi = i; bval = w[a][0]; }
-      }
-    }
-    publish(bv, bi, bval);
-  }
-  __syncthreads();
-  int info = 0;
-  for (int k = 0; k < n; ++k) {
-    float best = -1.0f, pv = 0.0f;
-    int p = n;
-#pragma unroll
-    for (int q = 0; q < NW; ++q) {
-      const float v = pmax[q];
-      const int i = pidx[q];
-      if (v > best || (v == best && i < p)) { best = v; p = i; pv = pval[q]; }
-    }
-    if (p >= n) {  // no candidate (NaN column): zero pivot on the lowest unused row
-      p = k;
-      pv = 0.0f;
-    }
-    const float pinv = (pv != 0.0f && isfinite(pv)) ? 1.0f / pv : 0.0f;
-    if (pinv == 0.0f && info == 0) info = k + 1;
-    if (c.tid == 0) c.piv[k] = p;
-    const int pa = p / TR, pt = p % TR;
-    const int kb = k / TC, kt = k % TC;
-    if (tr == pt) {
-#pragma unroll
-      for (int a = 0; a < RA; ++a)
-        if (a == pa) {
-#pragma unroll
-          for (int b = 0; b < CB; ++b) {
-            const int j = tc + TC * b;
-            const float v = (j == k ? 1.0f : w[a][b]) * pinv;
-            w[a][b] = v;
-            if (j < n) prow[j] = v;
-          }
-          used |= 1u << a;
-        }
-    }
-    if (tc == kt) {
-#pragma unroll
-      for (int b = 0; b < CB; ++b)
-        if (b == kb) {
-#pragma unroll
-          for (int a = 0; a < RA; ++a) {
-            const int i = tr + TR * a;
-            if (i < n) pcol[i] = w[a][b];
-          }
-        }
-    }
-    __syncthreads();
-    float pr[CB];
-#pragma unroll
-    for (int b = 0; b < CB; ++b) {
-      const int j = tc + TC * b;
-      pr[b] = j < n ? prow[j] : 0.0f;
-    }
-    const int cn = k + 1, cnb = cn / TC, cnt = cn % TC;
-    float bv = -1.0f, bval = 0.0f;
-    int bi = n;
-#pragma unroll
-    for (int a = 0; a < RA; ++a) {
-      const int i = tr + TR * a;
-      if (i < n && i != p) {
-        const float f = pcol[i];
-#pragma unroll
-        for (int b = 0; b < CB; ++b) {
-          const int j = tc + TC * b;
-          w[a][b] = (j == k ? 0.0f : w[a][b]) - f * pr[b];
-        }
-        if (tc == cnt && !((used >> a) & 1u)) {
-#pragma unroll
-          for (int b = 0; b < CB; ++b)
-            if (b == cnb) {
-              const float x = fabsf(w[a][b]);
-              if (x > bv || (x == bv && i < bi)) { bv = x; bi = i; bval = w[a][b]; }
-            }
-        }
-      }
-    }
-    publish(bv, bi, bval);
-    __syncthreads();
-  }
-  // inverse permutation of the pivot rows, then the scatter into the true inverse
-  for (int k = c.tid; k < n; k += NW * 32) c.perm[c.piv[k]] = k;
-  __syncthreads();
-#pragma unroll
-  for (int a = 0; a < RA; ++a)
-#pragma unroll
-    for (int b = 0; b < CB; ++b) {
-      const int i = tr + TR * a, j = tc + TC * b;
-      if (i < n && j < n) A[c.perm[i] * ld + c.piv[j]] = w[a][b];
-    }
-  __syncthreads();
-  return info;
-}
-
 // Gauss-Jordan inverse (FP32) with the matrix in registers, by columns: warp w owns
 // the columns j = w + NW c (c < CC), lane l the rows l + 32 s (s < RS). Partial
-// pivoting by index as in gj_invert_reg (the unused row with the largest |a_ik|,
-// lowest row index on ties; rows are not moved). The warp owning column k searches
-// it, publishes the pivot row p, 1/a_pk and the column (the multipliers) through
+// pivoting by index (the unused row with the largest |a_ik|, lowest row index on
+// ties; rows are not moved, the k-th pivot row is recorded instead). The warp
+// owning column k searches it, publishes the pivot row p, 1/a_pk and the column (the multipliers) through
 // shared memory (double-buffered), and every warp then broadcasts the pivot row's
 // values of its own columns by warp shuffles and updates them: one CTA barrier per
 // column. Column k is first replaced by the unit vector e_p, so it ends up holding
@@ -1443,9 +1294,10 @@ __device__ int factor(Cta<NW>& c, int n) {
       if (n <= 56) return gj_invert_wc<4, 2, 14>(c, A, n);
       if (n <= 64) return gj_invert_wc<4, 2, 16>(c, A, n);
     } else if constexpr (NW == 8) {
-      if (n <= 128) return gj_invert_reg<8, 16, 16, 8, 8>(c, A, n);
+      if (n <= 64) return gj_invert_wc<8, 2, 8>(c, A, n);
+      if (n <= 128) return gj_invert_wc<8, 4, 16>(c, A, n);
     } else if constexpr (NW == 2) {
-      if (n <= 64) return gj_invert_reg<2, 4, 16, 16, 4>(c, A, n);
+      if (n <= 64) return gj_invert_wc<2, 2, 32>(c, A, n);
     }
     return gj_invert<NW>(c, A, n);
   }

@@ -116,7 +116,7 @@ extern "C" chem_status chem_integrate_noalloc(chem_handle h, int64_t n_cells, do
   a.use_h0 = 0;
   a.smem_K = h->K;
   a.smem_I = h->I > 0 ? h->I : 1;
-  const int block = h->block;
+  const int block = h->block ? h->block : chem_internal_pick_block(h, a.smem_K, a.smem_I);
   int grid;
   if (a.sched == chem::SCHED_PLAIN) {
     grid = (int)n_cells;

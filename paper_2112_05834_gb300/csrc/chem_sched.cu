@@ -244,10 +244,7 @@ chem_status chem_internal_autotune(chem_handle h, const IntegrateArgs& a, cudaSt
     *block = cached;
     return CHEM_OK;
   }
-  if (a.n_jobs != 1 || a.perm) {  // tune single-job, index-ordered calls only
-    *block = h->block;
-    return CHEM_OK;
-  }
+  if (a.n_jobs != 1 || a.perm) return CHEM_OK;  // tune single-job, index-ordered calls only (keep *block)
   const Job& J = a.jobs[0];
   const int64_t S = std::min<int64_t>(J.n_cells, 4 * 1024);
   const int K = J.m.K;
@@ -267,7 +264,7 @@ chem_status chem_internal_autotune(chem_handle h, const IntegrateArgs& a, cudaSt
   cudaEventCreate(&ev1);
   const int cands[3] = {64, 128, 256};
   float best = 1e30f;
-  int best_b = h->block;
+  int best_b = *block;
   for (int b : cands) {
     IntegrateArgs t = a;
     t.n_total = S;

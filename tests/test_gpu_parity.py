@@ -282,6 +282,16 @@ def test_block_sizes(pkg, orc, block):
     _assert_bound(g["T"], g["Y"], ref, f"block={block}")
 
 
+@pytest.mark.parametrize("block", [0, 128, 256])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_block_sizes_101(pkg, orc, block, precision):
+    """100 species (n = 101): the register Gauss-Jordan of 256-thread blocks, the
+    shared-memory one of 128-thread blocks, and the automatic choice agree with the oracle."""
+    m, st, dt, ref = _oracle_ref(orc, "c100_262k", 161)
+    g = _run(pkg, m, st, dt, block=block, precision=precision)
+    _assert_bound(g["T"], g["Y"], ref, f"block={block} precision={precision}")
+
+
 def test_graph_replay(pkg, orc):
     m, st, dt, ref = _oracle_ref(orc, "h2_10_1k", 1000)
     integ = pkg.Integrator(m, graph=1)
