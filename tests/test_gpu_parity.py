@@ -319,16 +319,17 @@ def test_host_entry_point(pkg, orc):
 
 def test_multi_mechanism_single_launch(pkg, orc):
     """Four mechanisms (10, 32, 54, 100 species) in one launch give the same
-    per-cell results as four separate calls, and match the oracle."""
+    per-cell results as four separate calls with the same block size (the
+    reduction layout depends on it), and match the oracle."""
     names = [("h2_10", 1e-5, synth.ATM), ("c_32", 1e-6, 60e5), ("c_54", 1e-6, 60e5), ("c_100", 1e-6, 40e5)]
     jobs, singles, host = [], [], []
     dt = 1e-6
     for i, (nm, _, p) in enumerate(names):
         m = synth.mechanism_preset(nm)
         st = synth.gen_states(m, 97 + i, seed=10 + i, p=p, classes=synth.MIXED_CLASSES)
-        integ = pkg.Integrator(m)
+        integ = pkg.Integrator(m, block=256)
         jobs.append((integ, _dev(st.T), _dev(st.p), _dev(st.Y)))
-        singles.append(_run(pkg, m, st, dt))
+        singles.append(_run(pkg, m, st, dt, block=256))
         host.append((m, st))
     pkg.integrate_jobs(jobs, dt, RTOL, ATOL)
     torch.cuda.synchronize()
