@@ -38,6 +38,16 @@ RTOL, ATOL = 1e-8, 1e-12
 # sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained on GB300), 152 SMs,
 # 2 flop per FMA, 2070 MHz maximum SM clock. The driver's measured peaks have no FP64 entry.
 FP64_PEAK_TFLOPS = 2 * 152 * 2 * 2.070e9 / 1e12
+# FP32 peak derived the same way: 128 FFMA per cycle per SM
+FP32_PEAK_TFLOPS = 128 * 152 * 2 * 2.070e9 / 1e12
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
 
 
 def parse():
@@ -52,8 +62,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--forms", default="plain_fp64,headline")
-    ap.add_argument("--phases", action="store_true",
-                    help="one extra untimed step per form with per-phase cycle counters")
+    ap.add_argument("--sweep", action="store_true",
+                    help="per-cell time vs absolute tolerance for the FP64 form's classical variants "
+                         "(forward-difference Jacobian, elimination without pivoting); one JSON line each")
+    ap.add_argument("--no-phases", action="store_true",
+                    help="skip the extra untimed step per form with per-phase cycle counters")
     return ap.parse_args()
 
 
@@ -154,6 +167,46 @@ def kernel_traffic(n_cells):
     return per_cell * n_cells
 
 
+def phase_rooflines(m, hd, n, mlp_ms):
+    """Per-phase fractions of the headline launch: phase time = the phase's share of the
+    CTAs' cycles (option "profile") x the launch's CUDA-event time; algorithmic work per
+    Rosenbrock step x the launch's steps. Rates + Jacobian against the FP64 peak; the
+    FP32 Gauss-Jordan inverse and the FP32 products of the stage solves against the FP32
+    peak; MLP inference (timed alone) against the measured BF16 peak; state streaming
+    against the measured HBM bandwidth."""
+    K, I = m.n_species, m.n_reactions
+    nn = K + 1
+    n_tb = int(np.sum(m.rxn_type >= 1))
+    n_fo = int(np.sum(m.rxn_type >= 2))
+    ph = hd["phases"]
+    t = hd["kernel_ms"] / 1e3
+    steps = hd["substeps"]
+    peaks = measured_peaks()
+    out = {}
+    rhs = 41 * K + 22 * I + 2 * n_tb * K + 30 * n_fo
+    share = ph["rhs+jac data"] + ph["assembly"] + ph["stage rhs"]
+    w = (7 * rhs + 24 * I + 6 * nn * nn) * steps
+    a = w / (share * t) / 1e12
+    out["rates_jacobian"] = {"bound": "alu", "achieved": a, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": a / FP64_PEAK_TFLOPS, "time_share": share}
+    share = ph["factorisation"] + ph["stage solves"]
+    w = (nn ** 3 + 12 * 2 * nn * nn) * steps  # Gauss-Jordan inverse + 12 FP32 products (1 sweep)
+    a = w / (share * t) / 1e12
+    out["factor_solve_fp32"] = {"bound": "alu", "achieved": a, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                "frac": a / FP32_PEAK_TFLOPS, "time_share": share}
+    if mlp_ms:
+        w = 2.0 * n * ((K + 2) * 128 + 128 * 128 + 128 * 2)
+        a = w / (mlp_ms / 1e3) / 1e12
+        pk = peaks.get("bf16_tflops", 1900.0)
+        out["mlp_inference"] = {"bound": "tensor", "achieved": a, "peak": pk, "unit": "TFLOP/s", "frac": a / pk,
+                                "ms": mlp_ms}
+    b = n * (2 * K + 3) * 8.0
+    a = b / t / 1e9
+    pk = peaks.get("hbm_gbs", 6800.0)
+    out["state_streaming"] = {"bound": "hbm", "achieved": a, "peak": pk, "unit": "GB/s", "frac": a / pk}
+    return out
+
+
 def cpu_baseline(m, st, dt, seconds, seed=0):
     """Oracle on a bounded uniform sample of the workload's cells (all host cores)."""
     import oracle
@@ -240,7 +293,7 @@ def run_ours(args, rank, world):
         tot = integ.totals()
         results[name] = {"ms_total": ms, "kernel_ms": float(np.mean(kms)), "substeps": tot["substeps"],
                          "failed": tot["failed"], "rejects": tot["rejects"]}
-        if args.phases:
+        if not args.no_phases:
             integ.set_option("profile", 1)
             one(integ)
             torch.cuda.synchronize()
@@ -264,15 +317,61 @@ def run_ours(args, rank, world):
         if it >= args.warmup:
             e2e_times.append(t1 - t0)
     e2e_s = sum(e2e_times)
+    # MLP inference alone on the batch (untimed region; for its roofline)
+    mlp_ms = None
+    if learned and hasattr(learned, "predict"):
+        learned.predict(T0, p, Y0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            learned.predict(T0, p, Y0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mlp_ms = e0.elapsed_time(e1) / 5
     if world > 1:
         t = torch.tensor([results["headline"]["ms_total"], e2e_s], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         results["headline"]["ms_total"], e2e_s = float(t[0]), float(t[1])
-    return m, st, dt, n, results, clk, e2e_s, learned, head
+    return m, st, dt, n, results, clk, e2e_s, learned, head, mlp_ms
+
+
+def run_sweep(args):
+    """Per-cell device time vs atol (rtol 1e-6) on the FP64 form with: forward-difference
+    Jacobian + elimination without pivoting, analytical Jacobian + elimination without
+    pivoting, analytical Jacobian + partial-pivot LU, and the mixed form for comparison.
+    Each point: one warm-up and one timed launch (CUDA events) from the same state."""
+    import torch
+
+    import paper_2112_05834_gb300 as pkg
+
+    n = args.cells or 8192
+    m, st, dt = synth.workload(args.workload, n_cells=n)
+    dev = torch.device("cuda", 0)
+    T0, p, Y0 = (torch.tensor(a, device=dev) for a in (st.T, st.p, st.Y))
+    variants = [("fd_jacobian+no_pivoting", dict(precision=0, jacobian=1, pivoting=0)),
+                ("analytic+no_pivoting", dict(precision=0, jacobian=0, pivoting=0)),
+                ("analytic+lu", dict(precision=0, jacobian=0, pivoting=1)),
+                ("analytic+mixed", dict(precision=1))]
+    for atol in (1e-6, 1e-8, 1e-10, 1e-12):
+        for name, opt in variants:
+            integ = pkg.Integrator(m, scheduler=2, time_kernel=1, **opt)
+            for _ in range(2):
+                T, Y = T0.clone(), Y0.clone()
+                integ.integrate(T, p, Y, dt, 1e-6, atol)
+                ms = integ.kernel_ms()
+            tot = integ.totals()
+            print(json.dumps({"sweep": name, "workload": args.workload, "n_cells": n, "rtol": 1e-6, "atol": atol,
+                              "us_per_cell": 1e3 * ms / n, "kernel_ms": ms, "substeps": tot["substeps"],
+                              "rejects": tot["rejects"], "failed": tot["failed"]}), flush=True)
+            integ.close()
 
 
 def main():
     args = parse()
+    if args.sweep:
+        run_sweep(args)
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if world > 1:
@@ -299,7 +398,7 @@ def main():
                     "e2e": {"value": v, "unit": "cells*step/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
             print(json.dumps(line))
         return
-    m, st, dt, n, res, clk, e2e_s, learned, head = run_ours(args, rank, world)
+    m, st, dt, n, res, clk, e2e_s, learned, head, mlp_ms = run_ours(args, rank, world)
     if rank != 0:
         return
     hd = res["headline"]
@@ -346,6 +445,7 @@ def main():
         line["speedup_vs_plain_fp64"] = value / pv
     if "phases" in hd:
         line["phase_share"] = hd["phases"]
+        line["phase_roofline"] = phase_rooflines(m, hd, n, mlp_ms)
     # per step: the integration kernel, plus (learned form) per 65,536-cell chunk the
     # feature, two GEMM and head kernels of the MLP, and 3 counting-sort kernels
     chunks = (n + 65535) // 65536

@@ -193,7 +193,10 @@ chem_status chem_integrate_jobs(const chem_job* jobs, int32_t n_jobs, double dt,
  *                 2 = queue (persistent CTAs pulling cells from a device counter)
  *   "order"       0 = cell index order; 1 = learned cost order (needs a trained
  *                 model, see chem_mlp_*); 2 = last-call cost order
- *   "h0"          0 = starting-step heuristic; 1 = learned initial step
+ *   "h0"          0 = starting-step heuristic; 1 = learned initial step;
+ *                 2 = carried over: each cell starts from the step size the
+ *                 controller proposed after its last step in the handle's
+ *                 previous call of the same size (the heuristic otherwise)
  *   "max_steps"   step budget per cell (default 100000)
  *   "block"       threads per cell: 64, 128 or 256; 0 (default) = the size with
  *                 the most resident warps per SM for the mechanism and precision
@@ -203,6 +206,13 @@ chem_status chem_integrate_jobs(const chem_job* jobs, int32_t n_jobs, double dt,
  *   "autotune"    1 = time block sizes on a sample at the first call for a
  *                 new size and keep the fastest
  *   "profile"     1 = accumulate per-phase cycle counters (chem_get_phase_cycles)
+ *   "jacobian"    FP64 form (precision 0) only: 0 = analytical (default);
+ *                 1 = forward differences, column j from f(y + d_j e_j) with
+ *                 d_j = sqrt(eps) max(|y_j|, 1 K for T or 1e-6), n extra RHS
+ *                 evaluations per Jacobian (the classical alternative the paper's
+ *                 analytical Jacobian replaces); also used by chem_eval_jacobian
+ *   "pivoting"    FP64 form only: 1 = partial pivoting (default); 0 = Gaussian
+ *                 elimination without row interchanges (a zero pivot rejects the step)
  *   "time_kernel" 1 = record CUDA events on the stream around each integration
  *                 kernel launch (chem_get_kernel_ms); chem_integrate_noalloc
  *                 does not record them

@@ -379,7 +379,7 @@ def log_cells(integ, T, p, Y, dt, rtol=1e-8, atol=1e-12):
 def train_cost_model(integ, mech, workload, n_cells, dt, seed=7, epochs=20, batch=8192, lr=1e-3):
     """Trains a cost model on the logs of a separately seeded batch of the same
     workload distribution and switches the integrator to the learned order and
-    initial step. Returns True."""
+    initial step. Returns the attached model."""
     import torch
 
     from . import synth
@@ -395,4 +395,4 @@ def train_cost_model(integ, mech, workload, n_cells, dt, seed=7, epochs=20, batc
     model.attach(integ)
     integ.set_option("order", 1)
     integ.set_option("h0", 1)
-    return True
+    return model

@@ -528,9 +528,11 @@ static chem_status ensure_stats(chem_handle h, int64_t n) {
   release(h, h->d_rej);
   release(h, h->d_status);
   release(h, h->d_hfirst);
+  release(h, h->d_hlast);
   release(h, h->d_cost);
   h->d_sub = h->d_rej = h->d_status = nullptr;
-  h->d_hfirst = nullptr;
+  h->d_hfirst = h->d_hlast = nullptr;
+  h->hlast_valid = false;
   h->d_cost = nullptr;
   h->stats_cap = 0;
   const int64_t cap = std::max<int64_t>(n, 1024);
@@ -539,6 +541,7 @@ static chem_status ensure_stats(chem_handle h, int64_t n) {
   if ((s = chem_internal_alloc(h, &h->d_rej, cap * 4)) != CHEM_OK) return s;
   if ((s = chem_internal_alloc(h, &h->d_status, cap * 4)) != CHEM_OK) return s;
   if ((s = chem_internal_alloc(h, &h->d_hfirst, cap * 8)) != CHEM_OK) return s;
+  if ((s = chem_internal_alloc(h, &h->d_hlast, cap * 8)) != CHEM_OK) return s;
   if ((s = chem_internal_alloc(h, &h->d_cost, cap * 4)) != CHEM_OK) return s;
   h->stats_cap = cap;
   h->cost_valid = false;
@@ -558,7 +561,7 @@ static const OptionDef kOptions[] = {
     {"ir_sweeps", &chem_handle_s::ir_sweeps, 0, 3},
     {"scheduler", &chem_handle_s::scheduler, 0, 2},
     {"order", &chem_handle_s::order, 0, 2},
-    {"h0", &chem_handle_s::h0mode, 0, 1},
+    {"h0", &chem_handle_s::h0mode, 0, 2},
     {"max_steps", &chem_handle_s::max_steps, 1, 2147483647.0},
     {"block", &chem_handle_s::block, 0, 256},
     {"ctas_per_sm", &chem_handle_s::ctas_per_sm, 0, 64},
@@ -566,6 +569,8 @@ static const OptionDef kOptions[] = {
     {"autotune", &chem_handle_s::autotune, 0, 1},
     {"profile", &chem_handle_s::profile, 0, 1},
     {"time_kernel", &chem_handle_s::time_kernel, 0, 1},
+    {"jacobian", &chem_handle_s::jac_fd, 0, 1},
+    {"pivoting", &chem_handle_s::pivoting, 0, 1},
 };
 
 extern "C" chem_status chem_set_option(chem_handle h, const char* key, double value) {
@@ -639,7 +644,11 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
     J.st.h_first = h->d_hfirst;
     J.st.status = h->d_status;
     J.cost_out = h->d_cost;
-    J.h0 = nullptr;
+    J.st.h_last = h->d_hlast;
+    // carried-over initial steps: the previous call's proposals for the same cells
+    // (read at a cell's start, overwritten at its end by the same CTA)
+    J.h0 = (h->h0mode == 2 && h->hlast_valid && h->hlast_n == jobs[j].n_cells) ? h->d_hlast : nullptr;
+    if (J.h0) a.use_h0 = 1;
     h->last_n = jobs[j].n_cells;
     total += jobs[j].n_cells;
     Kmax = std::max(Kmax, h->K);
@@ -658,6 +667,8 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
   a.max_steps = h0->max_steps;
   a.sched = h0->scheduler;
   a.ir_sweeps = h0->ir_sweeps;
+  a.jac_fd = h0->jac_fd;
+  a.no_pivot = h0->pivoting ? 0 : 1;
   a.smem_K = Kmax;
   a.smem_I = std::max(Imax, 1);
   a.queue = static_cast<int*>(h0->d_queue);
@@ -701,6 +712,8 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
   for (int j = 0; j < n_jobs; ++j) {
     jobs[j].h->cost_valid = true;
     jobs[j].h->cost_n = jobs[j].n_cells;
+    jobs[j].h->hlast_valid = true;
+    jobs[j].h->hlast_n = jobs[j].n_cells;
   }
   return CHEM_OK;
 }
@@ -897,7 +910,8 @@ extern "C" chem_status chem_eval_jacobian(chem_handle h, int64_t n, const double
                                           const double* Y, double* J, void* stream) {
   if (!h || n < 0 || (n > 0 && (!T || !p || !Y || !J))) return CHEM_ERR_INVALID_ARG;
   if (n == 0) return CHEM_OK;
-  CHEM_CUDA(h, launch_diag(h->dm, n, T, p, Y, J, 0, 0, 0, 1, h->precision, static_cast<cudaStream_t>(stream)));
+  CHEM_CUDA(h, launch_diag(h->dm, n, T, p, Y, J, 0, 0, 0, 1, h->precision, static_cast<cudaStream_t>(stream),
+                           h->jac_fd));
   return CHEM_OK;
 }
 

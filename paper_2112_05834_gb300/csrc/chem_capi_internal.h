@@ -36,6 +36,8 @@ struct chem_handle_s {
   int profile = 0;
   unsigned long long* d_phase = nullptr;  // [8] per-phase cycle counters (option "profile")
   int time_kernel = 0;                    // option "time_kernel": events around the integration launch
+  int jac_fd = 0;                         // option "jacobian": 1 = forward differences (FP64 form)
+  int pivoting = 1;                       // option "pivoting": 0 = no row interchanges (FP64 form)
   cudaEvent_t kev0 = nullptr, kev1 = nullptr;
   bool kev_recorded = false;
   // per-cell statistics of the last call
@@ -45,6 +47,9 @@ struct chem_handle_s {
   int32_t* d_rej = nullptr;
   int32_t* d_status = nullptr;
   double* d_hfirst = nullptr;
+  double* d_hlast = nullptr;  // controller's proposal after each cell's last step (option h0 = 2)
+  bool hlast_valid = false;
+  int64_t hlast_n = 0;
   float* d_cost = nullptr;  // substeps of the last call, for cost ordering
   bool cost_valid = false;
   int64_t cost_n = 0;

@@ -74,6 +74,7 @@ struct CellStats {
   int32_t* rejects;
   double* h_first;
   int32_t* status;
+  double* h_last;  // optional: step size the controller proposes after the cell's last step
 };
 
 struct Job {
@@ -99,6 +100,8 @@ struct IntegrateArgs {
   int sched;
   int ir_sweeps;
   int use_h0;          // 1: take jobs[j].h0 when finite and positive
+  int jac_fd;          // FP64 form only: 1 = forward-difference Jacobian (n extra RHS evaluations)
+  int no_pivot;        // FP64 form only: 1 = Gaussian elimination without row interchanges
   int smem_K, smem_I;  // sizes the shared-memory carve-up was computed for
   unsigned long long* phase;  // optional [8] per-phase cycle counters (diagnostic)
 };

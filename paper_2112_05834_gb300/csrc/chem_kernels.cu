@@ -932,7 +932,7 @@ __device__ __forceinline__ void warp_argmax_store(float v, int i, int lane, floa
 // inverse diagonal of U for the solves. Returns 0 or 1 + k for a zero pivot.
 // ---------------------------------------------------------------------------
 template <int NW, class R>
-__device__ int lu_factor(Cta<NW>& c, R* a, int n) {
+__device__ int lu_factor(Cta<NW>& c, R* a, int n, bool pivot = true) {
   constexpr int NT = NW * 32;
   const int ld = odd_ld(n);
   float* pmax = reinterpret_cast<float*>(c.red + SC_PIV);
@@ -951,7 +951,7 @@ __device__ int lu_factor(Cta<NW>& c, R* a, int n) {
   }
   __syncthreads();
   for (int k = 0; k < n; ++k) {
-    int p = pivot_reduce<NW>(c, pmax, pidx, n);
+    int p = pivot ? pivot_reduce<NW>(c, pmax, pidx, n) : k;  // no pivoting: the diagonal
     if (p >= n) p = k;  // a column of NaN: the zero-pivot path below
     if (c.tid == 0) {
       c.piv[k] = p;
@@ -1285,9 +1285,9 @@ __device__ void solve(Cta<NW>& c, int n, const double* b, double* x, int ir) {
 
 // Factorisation of the iteration matrix: LU (FP64 form) or the FP32 inverse.
 template <int NW, int PREC>
-__device__ int factor(Cta<NW>& c, int n) {
+__device__ int factor(Cta<NW>& c, int n, bool pivot = true) {
   if constexpr (!Policy<PREC>::IR) {
-    return lu_factor<NW, double>(c, reinterpret_cast<double*>(c.M), n);
+    return lu_factor<NW, double>(c, reinterpret_cast<double*>(c.M), n, pivot);
   } else {
     float* A = reinterpret_cast<float*>(c.M);
     if constexpr (NW == 4) {
@@ -1318,6 +1318,30 @@ __device__ void build_matrix(const DevMech& m, Cta<NW>& c, const Scal& s, const 
     float* dst = reinterpret_cast<float*>(c.M);
     for (int i = c.warp; i < n; i += NW)
       for (int j = c.lane; j < n; j += 32) dst[i * ld + j] = (float)src[i * ld + j];
+    __syncthreads();
+  }
+}
+
+// Iteration matrix (FP64 form) from a forward-difference Jacobian, column by column:
+// J_.j = (f(y + d_j e_j) - f(y)) / d_j with d_j = sqrt(eps) max(|y_j|, floor_j)
+// (floor 1 K for T, 1e-6 for mass fractions: a smaller floor lets rounding in f
+// dominate the columns of trace species); S = sg J + fac I as in assemble.
+// Costs n RHS evaluations: the classical alternative to the analytical Jacobian.
+template <int NW, bool JO>
+__device__ void fd_matrix(const DevMech& m, Cta<NW>& c, double p, const double* y, const double* f0, double fac) {
+  constexpr int NT = NW * 32;
+  const int n = m.K + 1, ld = odd_ld(n);
+  double* A = reinterpret_cast<double*>(c.M);
+  for (int j = 0; j < n; ++j) {
+    const double d = 1.4901161193847656e-8 * fmax(fabs(y[j]), j == 0 ? 1.0 : 1e-6);
+    for (int i = c.tid; i < n; i += NT) c.ys[i] = y[i] + (i == j ? d : 0.0);
+    __syncthreads();
+    eval_rhs<NW, false, false>(m, c, c.ys, p, c.fv);
+    const double id = 1.0 / d;
+    for (int i = c.tid; i < n; i += NT) {
+      const double J = (c.fv[i] - f0[i]) * id;
+      A[i * ld + j] = JO ? J : -J + (i == j ? fac : 0.0);
+    }
     __syncthreads();
   }
 }
@@ -1426,7 +1450,7 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
     if (part[0] > 0.0 || !(c.y[0] > 0.0) || !(p > 0.0)) status = CHEM_CELL_NONFINITE;
   }
   int steps = 0, rejects = 0;
-  double h_first = 0.0;
+  double h_first = 0.0, h_next = 0.0;
   if (status == CHEM_CELL_OK) {
     double h_target, cp_dummy;
     h_cp_mass(m, c, c.y[0], c.y + 1, h_target, cp_dummy);
@@ -1440,21 +1464,28 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
       eval_rhs<NW, false, Policy<PREC>::IR>(m, c, c.y, p, c.f0);
       h = starting_step<NW, Policy<PREC>::IR>(m, c, p, dt, rtol, atol);
     }
-    double t = 0.0;
+    double t = 0.0, h_unclipped = h;
     bool after_reject = false;
     while (true) {
       if (dt - t <= 1e-12 * dt) break;
       if (steps >= args.max_steps) { status = CHEM_CELL_MAX_STEPS; break; }
       if (!(h >= kHmin)) { status = CHEM_CELL_H_UNDERFLOW; break; }  // also catches NaN
+      h_unclipped = h;
       if (t + h > dt) h = dt - t;
       ++steps;
       // Jacobian and f0 at y; iteration matrix; factorisation
       PHASE(1);
-      const Scal s = eval_rhs<NW, true, Policy<PREC>::IR>(m, c, c.y, p, c.f0);
-      PHASE(2);
-      build_matrix<NW, PREC, false>(m, c, s, c.f0, 1.0 / (h * kRodasGamma));
+      if (PREC == PREC_FP64 && args.jac_fd) {
+        eval_rhs<NW, false, false>(m, c, c.y, p, c.f0);
+        PHASE(2);
+        fd_matrix<NW, false>(m, c, p, c.y, c.f0, 1.0 / (h * kRodasGamma));
+      } else {
+        const Scal s = eval_rhs<NW, true, Policy<PREC>::IR>(m, c, c.y, p, c.f0);
+        PHASE(2);
+        build_matrix<NW, PREC, false>(m, c, s, c.f0, 1.0 / (h * kRodasGamma));
+      }
       PHASE(3);
-      const int info = factor<NW, PREC>(c, n);
+      const int info = factor<NW, PREC>(c, n, !(PREC == PREC_FP64 && args.no_pivot));
       PHASE(6);
       double err, step_fac = kFacMin;
       if (info != 0) {
@@ -1511,6 +1542,9 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
       after_reject = false;
       h *= fac;
     }
+    // step size to carry to the next call: the controller's proposal, or the step
+    // before the final clipping to dt when that was longer
+    h_next = fmax(h, h_unclipped);
     // temperature from the conserved mass enthalpy (Newton, |dT| < 1e-10 T)
     PHASE(7);
     if (status == CHEM_CELL_OK) {
@@ -1538,6 +1572,7 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
     if (job.st.rejects) job.st.rejects[cell] = rejects;
     if (job.st.h_first) job.st.h_first[cell] = h_first;
     if (job.st.status) job.st.status[cell] = status;
+    if (job.st.h_last) job.st.h_last[cell] = status == CHEM_CELL_OK ? h_next : 0.0;
     if (job.cost_out) job.cost_out[cell] = (float)steps;
   }
   __syncthreads();
@@ -1583,7 +1618,8 @@ struct DiagArgs {
   const double *T, *p, *Y;
   double* out;
   double dt, rtol, atol;
-  int what;  // 0 rhs, 1 jacobian, 2 h0
+  int what;    // 0 rhs, 1 jacobian, 2 h0
+  int jac_fd;  // FP64 form: forward-difference Jacobian for what = 1
 };
 
 template <int NW, int PREC>
@@ -1605,8 +1641,13 @@ __global__ void __launch_bounds__(NW * 32) k_diag(const __grid_constant__ DiagAr
       eval_rhs<NW, false, Policy<PREC>::IR>(a.m, c, c.y, p, c.f0);
       for (int i = c.tid; i < n; i += NT) a.out[(size_t)cell * n + i] = c.f0[i];
     } else if (a.what == 1) {
-      const Scal s = eval_rhs<NW, true, Policy<PREC>::IR>(a.m, c, c.y, p, c.f0);
-      build_matrix<NW, PREC, true>(a.m, c, s, c.f0, 0.0);
+      if (PREC == PREC_FP64 && a.jac_fd) {
+        eval_rhs<NW, false, false>(a.m, c, c.y, p, c.f0);
+        fd_matrix<NW, true>(a.m, c, p, c.y, c.f0, 0.0);
+      } else {
+        const Scal s = eval_rhs<NW, true, Policy<PREC>::IR>(a.m, c, c.y, p, c.f0);
+        build_matrix<NW, PREC, true>(a.m, c, s, c.f0, 0.0);
+      }
       const A* J = reinterpret_cast<const A*>(Policy<PREC>::IR ? c.M0 : c.M);
       for (int i = c.warp; i < n; i += NW)
         for (int j = c.lane; j < n; j += 32) a.out[(size_t)cell * n * n + i * n + j] = (double)J[i * ld + j];
@@ -1726,8 +1767,9 @@ static cudaError_t launch_simple(KernelT k, const ArgT& a, size_t smem, int grid
 
 cudaError_t launch_diag(const DevMech& m, int64_t n, const double* T, const double* p, const double* Y,
                         double* out, double dt, double rtol, double atol, int what, int prec,
-                        cudaStream_t st) {
+                        cudaStream_t st, int jac_fd) {
   DiagArgs a;
+  a.jac_fd = jac_fd;
   a.m = m;
   a.n = n;
   a.T = T;

@@ -113,6 +113,8 @@ extern "C" chem_status chem_integrate_noalloc(chem_handle h, int64_t n_cells, do
   a.max_steps = h->max_steps;
   a.sched = h->scheduler;
   a.ir_sweeps = h->ir_sweeps;
+  a.jac_fd = h->jac_fd;
+  a.no_pivot = h->pivoting ? 0 : 1;
   a.use_h0 = 0;
   a.smem_K = h->K;
   a.smem_I = h->I > 0 ? h->I : 1;

@@ -109,7 +109,7 @@ chem_status chem_internal_cost_order(chem_handle h, const float* d_cost, int64_t
 
 chem_status chem_internal_prepare_learned(chem_handle h, const chem_job* jobs, int32_t n_jobs, IntegrateArgs* a,
                                           cudaStream_t st) {
-  if (h->order == 0 && h->h0mode == 0) return CHEM_OK;
+  if (h->order == 0 && h->h0mode != 1) return CHEM_OK;
   if (n_jobs != 1) {
     h->err = "order/h0 options apply to single-mechanism calls";
     return CHEM_ERR_INVALID_ARG;
@@ -273,6 +273,8 @@ chem_status chem_internal_autotune(chem_handle h, const IntegrateArgs& a, cudaSt
     t.jobs[0].p = work + S;
     t.jobs[0].Y = work + 2 * S;
     t.jobs[0].cost_out = nullptr;
+    t.jobs[0].st.h_last = nullptr;  // keep the carried-over steps of the real call intact
+    t.jobs[0].h0 = nullptr;
     int occ = 0;
     if (occupancy_integrate(b, h->precision, a.smem_K, a.smem_I, &occ) != cudaSuccess || occ < 1) continue;
     const int grid = (int)std::min<int64_t>(S, (int64_t)occ * h->num_sms);

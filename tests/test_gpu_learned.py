@@ -173,3 +173,49 @@ def test_cfd_loop_learned(pkg):
         assert np.all(np.abs(Yg[pick] - ref["Y"]) <= 1e-8 + 1e-5 * np.abs(ref["Y"])), step
         print("step", step + 1, "substeps", int(s["substeps"].sum()))
         st = synth.perturb_states(synth.CellStates(T=Tg, p=st.p, Y=Yg, kind=st.kind), seed=100 + step)
+
+
+def test_carry_over_h0(pkg):
+    """Option h0 = 2 (the OpenFOAM-style stored step, a baseline for the learned h0):
+    with no history the call equals the heuristic bitwise; on the next CFD step
+    (perturbed states of the same cells) every cell starts from the step its controller
+    proposed last time and stays within the parity bound. Its cost against the
+    heuristic is reported: the perturbation re-excites fast transients, so the
+    carried-over step may cost rejections; it must not cost more than 25 % steps."""
+    import oracle
+
+    oracle.build()
+    n = 4096
+    m, st, dt = synth.workload("c54_65k", n_cells=n, state_seed=47)
+    heur = pkg.Integrator(m, precision=1, scheduler=2)
+    carry = pkg.Integrator(m, precision=1, scheduler=2, h0=2)
+    first = {}
+    for name, integ in (("heur", heur), ("carry", carry)):
+        T, p, Y = _dev(st.T), _dev(st.p), _dev(st.Y)
+        integ.integrate(T, p, Y, dt, RTOL, ATOL)
+        first[name] = (T.cpu().numpy(), Y.cpu().numpy())
+    np.testing.assert_array_equal(first["heur"][0], first["carry"][0])
+    np.testing.assert_array_equal(first["heur"][1], first["carry"][1])
+    st2 = synth.perturb_states(synth.CellStates(T=first["heur"][0], p=st.p, Y=first["heur"][1], kind=st.kind),
+                               seed=48)
+    out = {}
+    for name, integ in (("heur", heur), ("carry", carry)):
+        T, p, Y = _dev(st2.T), _dev(st2.p), _dev(st2.Y)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        integ.integrate(T, p, Y, dt, RTOL, ATOL)
+        torch.cuda.synchronize()
+        s = integ.stats(n)
+        out[name] = {"T": T.cpu().numpy(), "Y": Y.cpu().numpy(), "time": time.perf_counter() - t0,
+                     "substeps": s["substeps"].cpu().numpy(), "status": s["status"].cpu().numpy()}
+        assert np.all(out[name]["status"] == 0)
+    rng = np.random.default_rng(3)
+    pick = np.unique(np.concatenate([rng.choice(n, 24, replace=False), np.argsort(out["carry"]["substeps"])[-8:]]))
+    ref = oracle.integrate(m, st2.T[pick], st2.p[pick], st2.Y[pick], dt, RTOL, ATOL)
+    for name, o in out.items():
+        assert np.all(np.abs(o["T"][pick] - ref["T"]) <= 1e-6 * ref["T"]), name
+        assert np.all(np.abs(o["Y"][pick] - ref["Y"]) <= 1e-8 + 1e-5 * np.abs(ref["Y"])), name
+    sh, sc = int(out["heur"]["substeps"].sum()), int(out["carry"]["substeps"].sum())
+    print("step 2 substeps heuristic", sh, "carried", sc, "RHS evaluations", 7 * sh + 2 * n, "vs", 7 * sc,
+          "time %.4f vs %.4f s" % (out["heur"]["time"], out["carry"]["time"]))
+    assert sc <= 1.25 * sh

@@ -103,6 +103,38 @@ def test_jacobian_parity(pkg, orc, name):
             assert err.max() <= tol, (name, precision, c, err.max())
 
 
+@pytest.mark.parametrize("name", ["h2_10", "c_54"])
+def test_fd_jacobian_vs_oracle(pkg, orc, name):
+    """Option jacobian = 1 (forward differences, FP64 form) against the oracle's
+    analytical Jacobian: truncation (the quadratic and third-body terms) and rounding
+    of a forward difference leave each entry within 5e-3 of its row's largest entry
+    (the same difference quotient on the oracle's RHS: 2.8e-3 and 1.6e-3)."""
+    m = _mech_cases()[name]
+    st = _states(m, n=12)
+    M = orc.Mech(m)
+    integ = pkg.Integrator(m, precision=0, jacobian=1)
+    J = integ.eval_jacobian(_dev(st.T), _dev(st.p), _dev(st.Y)).cpu().numpy()
+    worst = 0.0
+    for c in range(st.T.shape[0]):
+        y = np.concatenate([[st.T[c]], st.Y[c]])
+        Jr = orc.jac(M, st.p[c], y)
+        row = np.abs(Jr).max(axis=1, keepdims=True) + 1e-300
+        worst = max(worst, (np.abs(J[c] - Jr) / row).max())
+    print(name, "forward-difference Jacobian: max error / row max", worst)
+    assert worst <= 5e-3
+
+
+@pytest.mark.parametrize("jacobian,pivoting", [(1, 1), (0, 0), (1, 0)])
+def test_fd_and_naive_elimination_parity(pkg, orc, jacobian, pivoting):
+    """The classical variants of the FP64 form (forward-difference Jacobian and/or
+    Gaussian elimination without row interchanges) integrate within the parity bound."""
+    for name, n in (("h2_10_1k", 200), ("c54_65k", 64)):
+        m, st, dt, ref = _oracle_ref(orc, name, n)
+        g = _run(pkg, m, st, dt, precision=0, jacobian=jacobian, pivoting=pivoting)
+        assert np.all(g["status"] == 0)
+        _assert_bound(g["T"], g["Y"], ref, f"{name} jacobian={jacobian} pivoting={pivoting}")
+
+
 def test_starting_step_parity(pkg, orc):
     m = synth.mechanism_preset("c_54")
     st = _states(m, n=32)
