@@ -689,7 +689,10 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
     h0->err = "chem_integrate: mechanism too large for shared memory";
     return CHEM_ERR_INVALID_ARG;
   }
-  int block = h0->block ? h0->block : chem_internal_pick_block(h0, a.smem_K, a.smem_I);
+  // the mixed form may keep its FP64 matrix in global memory on persistent grids when
+  // that lets more CTAs share an SM (large mechanisms)
+  const bool m0g_ok = h0->precision == PREC_MIXED && a.sched != SCHED_PLAIN;
+  int block = h0->block ? h0->block : chem_internal_pick_block(h0, a.smem_K, a.smem_I, m0g_ok);
   if (h0->autotune) {
     s = chem_internal_autotune(h0, a, st, &block);
     if (s != CHEM_OK) return s;
@@ -700,12 +703,39 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
   } else {
     int occ = 0;
     CHEM_CUDA(h0, occupancy_integrate(block, h0->precision, a.smem_K, a.smem_I, &occ));
+    bool m0g = false;
+    if (m0g_ok) {
+      int occ_g = 0;
+      CHEM_CUDA(h0, occupancy_integrate(block, h0->precision, a.smem_K, a.smem_I, &occ_g, true));
+      if (occ_g > occ) {
+        occ = occ_g;
+        m0g = true;
+      }
+    }
     if (occ < 1) {
       h0->err = "chem_integrate: kernel does not fit on an SM";
       return CHEM_ERR_CUDA;
     }
     if (h0->ctas_per_sm > 0) occ = std::min(occ, h0->ctas_per_sm);
     grid = (int)std::min<int64_t>(total, (int64_t)occ * h0->num_sms);
+    if (m0g) {
+      const int nmax = a.smem_K + 1;
+      const int64_t stride = (int64_t)nmax * (nmax | 1);
+      const size_t bytes = (size_t)grid * stride * sizeof(double);
+      if (bytes > h0->m0_cap) {
+        cudaStreamSynchronize(st);
+        if (h0->d_m0) {
+          release(h0, h0->d_m0);
+          h0->d_m0 = nullptr;
+          h0->m0_cap = 0;
+        }
+        s = chem_internal_alloc(h0, &h0->d_m0, bytes);
+        if (s != CHEM_OK) return s;
+        h0->m0_cap = bytes;
+      }
+      a.m0_scratch = h0->d_m0;
+      a.m0_stride = stride;
+    }
   }
   s = chem_internal_launch(h0, a, block, grid, st);
   if (s != CHEM_OK) return s;
@@ -720,7 +750,7 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
 
 // Block size with the most resident warps per SM for this mechanism size and
 // precision (ties: 128, then 64, then 256 threads).
-int chem_internal_pick_block(chem_handle h, int K, int I) {
+int chem_internal_pick_block(chem_handle h, int K, int I, bool allow_m0_global) {
   int best = 128, best_w = -1;
   for (int b : {128, 64, 256}) {
     int occ = 0;
@@ -728,6 +758,10 @@ int chem_internal_pick_block(chem_handle h, int K, int I) {
       cudaGetLastError();
       continue;
     }
+    int occ_g = 0;
+    if (allow_m0_global && occupancy_integrate(b, h->precision, K, I, &occ_g, true) == cudaSuccess)
+      occ = std::max(occ, occ_g);
+    cudaGetLastError();
     if (occ * b / 32 > best_w) {
       best_w = occ * b / 32;
       best = b;

@@ -35,6 +35,8 @@ struct chem_handle_s {
   int autotune = 0;
   int profile = 0;
   unsigned long long* d_phase = nullptr;  // [8] per-phase cycle counters (option "profile")
+  double* d_m0 = nullptr;                 // per-CTA slots of the mixed form's FP64 matrix (large mechanisms)
+  size_t m0_cap = 0;                      // bytes
   int time_kernel = 0;                    // option "time_kernel": events around the integration launch
   int jac_fd = 0;                         // option "jacobian": 1 = forward differences (FP64 form)
   int pivoting = 1;                       // option "pivoting": 0 = no row interchanges (FP64 form)
@@ -78,7 +80,7 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
                                     cudaStream_t st);
 chem_status chem_internal_launch(chem_handle h, const chem::IntegrateArgs& a, int block, int grid,
                                  cudaStream_t st);
-int chem_internal_pick_block(chem_handle h, int K, int I);
+int chem_internal_pick_block(chem_handle h, int K, int I, bool allow_m0_global = false);
 chem_status chem_internal_graph_launch(chem_handle h, const chem::IntegrateArgs& a, int block, int grid,
                                        cudaStream_t st);
 chem_status chem_internal_autotune(chem_handle h, const chem::IntegrateArgs& a, cudaStream_t st, int* block);

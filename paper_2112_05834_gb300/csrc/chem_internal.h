@@ -104,6 +104,8 @@ struct IntegrateArgs {
   int no_pivot;        // FP64 form only: 1 = Gaussian elimination without row interchanges
   int smem_K, smem_I;  // sizes the shared-memory carve-up was computed for
   unsigned long long* phase;  // optional [8] per-phase cycle counters (diagnostic)
+  double* m0_scratch;  // mixed form, persistent grids: per-CTA slots for the FP64 assembled
+  int64_t m0_stride;   //   matrix (null: it stays in shared memory); doubles per slot
 };
 
 }  // namespace chem

@@ -354,7 +354,9 @@ __host__ __device__ inline int odd_ld(int n) { return n | 1; }
 // vectors (double): y, yn, ys, f0, fv, rr, u[6], sc  -> 13 n
 // species (double): C, hRT, cpR, eg, dcp, dk, akT, ek, ieg -> 9 K
 // reactions (double): q, D, dTc, P, dqs[4] -> 8 I
-__host__ __device__ inline Layout make_layout(int Kmax, int Imax, int prec) {
+// m0_global: the mixed form's FP64 assembled matrix lives in a global-memory slot of
+// the CTA instead of shared memory (large mechanisms, persistent schedulers).
+__host__ __device__ inline Layout make_layout(int Kmax, int Imax, int prec, bool m0_global = false) {
   Layout L;
   L.nmax = Kmax + 1;
   L.ld = odd_ld(L.nmax);
@@ -384,7 +386,7 @@ __host__ __device__ inline Layout make_layout(int Kmax, int Imax, int prec) {
   }
   o = (o + 15) & ~(size_t)15;
   L.off_M0 = o;
-  if (prec == PREC_MIXED) o += (size_t)L.nmax * L.ld * sizeof(double);
+  if (prec == PREC_MIXED && !m0_global) o += (size_t)L.nmax * L.ld * sizeof(double);
   if (prec == PREC_FP32ASM) o += (size_t)L.nmax * L.ld * sizeof(float);
   o = (o + 15) & ~(size_t)15;
   L.off_piv = o;
@@ -395,7 +397,9 @@ __host__ __device__ inline Layout make_layout(int Kmax, int Imax, int prec) {
   return L;
 }
 
-size_t smem_bytes(int Kmax, int Imax, int prec) { return make_layout(Kmax, Imax, prec).total; }
+size_t smem_bytes(int Kmax, int Imax, int prec, bool m0_global) {
+  return make_layout(Kmax, Imax, prec, m0_global).total;
+}
 
 // Scalars kept in the reduction area (after the 4 x NW partial-sum slots).
 // SC_OUT: 8 broadcast results of Cta::reduce; SC_PIV: pivot search slots (12 NW bytes)
@@ -1581,15 +1585,19 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
-// Four CTAs of 128 threads per SM fit the register file at 128 registers a thread,
-// matching what the shared-memory footprint allows for mechanisms up to ~60 species.
+// Launch bounds keep 128 registers a thread: four CTAs of 128 threads, eight of 64 or
+// two of 256 fill the register file. Four CTAs of 128 threads also match what the
+// shared-memory footprint allows for mechanisms up to ~60 species; the larger counts
+// need the global-memory slot for the mixed form's FP64 matrix.
 template <int NW, int PREC>
-__global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : 1) k_integrate(const __grid_constant__ IntegrateArgs args) {
+__global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : NW == 2 ? 8 : 2) k_integrate(const __grid_constant__ IntegrateArgs args) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long s_work;
-  const Layout L = make_layout(args.smem_K, args.smem_I, PREC);
+  const bool m0g = PREC == PREC_MIXED && args.m0_scratch != nullptr;
+  const Layout L = make_layout(args.smem_K, args.smem_I, PREC, m0g);
   Cta<NW> c;
   c.bind(smem, L);
+  if (m0g) c.M0 = args.m0_scratch + (size_t)blockIdx.x * args.m0_stride;
   c.load_tables();  // first read after the barrier that ends each cell's state load
   for (long long it = 0;; ++it) {
     long long w;
@@ -1714,7 +1722,7 @@ static cudaError_t prep(KernelT k, size_t smem) {
 
 template <int NW, int PREC>
 static cudaError_t launch_integrate_t(const IntegrateArgs& a, int grid, cudaStream_t st) {
-  const size_t smem = smem_bytes(a.smem_K, a.smem_I, PREC);
+  const size_t smem = smem_bytes(a.smem_K, a.smem_I, PREC, a.m0_scratch != nullptr);
   cudaError_t e = prep(k_integrate<NW, PREC>, smem);
   if (e != cudaSuccess) return e;
   k_integrate<NW, PREC><<<grid, NW * 32, smem, st>>>(a);
@@ -1734,8 +1742,8 @@ cudaError_t launch_integrate(const IntegrateArgs& a, int block, int prec, int gr
 #undef LI
 }
 
-cudaError_t occupancy_integrate(int block, int prec, int K, int I, int* ctas_per_sm) {
-  const size_t smem = smem_bytes(K, I, prec);
+cudaError_t occupancy_integrate(int block, int prec, int K, int I, int* ctas_per_sm, bool m0_global) {
+  const size_t smem = smem_bytes(K, I, prec, m0_global);
   cudaError_t e;
 #define OCC(NW, P)                                                                         \
   do {                                                                                     \

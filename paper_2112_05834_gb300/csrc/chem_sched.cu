@@ -174,7 +174,7 @@ chem_status chem_internal_graph_launch(chem_handle h, const IntegrateArgs& a, in
       }
     }
     int occ = 0;
-    occupancy_integrate(block, h->precision, a.smem_K, a.smem_I, &occ);  // sets kernel attributes
+    occupancy_integrate(block, h->precision, a.smem_K, a.smem_I, &occ, a.m0_scratch != nullptr);  // sets kernel attributes
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess && a.sched == SCHED_QUEUE) e = cudaMemsetAsync(a.queue, 0, sizeof(int), h->cap_stream);
@@ -274,6 +274,7 @@ chem_status chem_internal_autotune(chem_handle h, const IntegrateArgs& a, cudaSt
     t.jobs[0].Y = work + 2 * S;
     t.jobs[0].cost_out = nullptr;
     t.jobs[0].st.h_last = nullptr;  // keep the carried-over steps of the real call intact
+    t.m0_scratch = nullptr;         // trials keep the FP64 matrix in shared memory
     t.jobs[0].h0 = nullptr;
     int occ = 0;
     if (occupancy_integrate(b, h->precision, a.smem_K, a.smem_I, &occ) != cudaSuccess || occ < 1) continue;
