@@ -65,6 +65,14 @@ def parse():
     ap.add_argument("--sweep", action="store_true",
                     help="per-cell time vs absolute tolerance for the FP64 form's classical variants "
                          "(forward-difference Jacobian, elimination without pivoting); one JSON line each")
+    ap.add_argument("--cfd-loop", action="store_true",
+                    help="the learned scheduling configuration: 100 species, 1,048,576 cells, 20 CFD steps "
+                         "with mixing between steps, training on steps 1-5; one JSON line per step")
+    ap.add_argument("--retrain-every", type=int, default=0,
+                    help="with --cfd-loop: retrain the model every N steps on the learned form's own logs "
+                         "of the last N steps (0: train once, on steps 1-5)")
+    ap.add_argument("--no-learned-order", action="store_true",
+                    help="with --cfd-loop: learned initial step only, index order")
     ap.add_argument("--no-phases", action="store_true",
                     help="skip the extra untimed step per form with per-phase cycle counters")
     return ap.parse_args()
@@ -367,10 +375,95 @@ def run_sweep(args):
             integ.close()
 
 
+def run_cfd_loop(args):
+    """Learned scheduling + initial step at scale: the 100-species mechanism, 1,048,576
+    cells (or --cells), 20 CFD steps of dt with the seeded mixing perturbation between
+    steps. Steps 1-5 run the plain heuristic in index order and log per-cell substeps
+    and first accepted steps; the MLP trains on those logs (timed, reported apart);
+    steps 6-20 run the learned order and initial step. Every step also runs the plain
+    form on the identical input, so the gain is measured on the same states. Mixed
+    precision, work queue; CUDA events around each integrate call (MLP inference and
+    the cost sort included)."""
+    import torch
+
+    import paper_2112_05834_gb300 as pkg
+
+    n = args.cells or 1048576
+    m, st, dt = synth.workload("c100_1m", n_cells=n)
+    dev = torch.device("cuda", 0)
+    plain = pkg.Integrator(m, precision=1, scheduler=2)
+    learned = pkg.Integrator(m, precision=1, scheduler=2)
+    model = pkg.CostModel(m.n_species, seed=11)
+    logs = []
+    tot = {"plain_ms": 0.0, "learned_ms": 0.0, "plain_sub": 0, "learned_sub": 0}
+
+    def timed(integ, T0, p, Y0):
+        T, Y = T0.clone(), Y0.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        integ.integrate(T, p, Y, dt, RTOL, ATOL)
+        e1.record()
+        torch.cuda.synchronize()
+        s = integ.stats(n)
+        return T, Y, e0.elapsed_time(e1), s
+
+    for step in range(1, 21):
+        T0, p, Y0 = (torch.tensor(a, device=dev) for a in (st.T, st.p, st.Y))
+        line = {"cfd_step": step, "n_cells": n}
+        if step == 6:
+            t0 = time.perf_counter()
+            cat = [torch.cat([lg[k] for lg in logs]) for k in range(5)]
+            losses = model.train(*cat, epochs=20, batch=8192, lr=1e-3, seed=12)
+            torch.cuda.synchronize()
+            line["train_s"] = time.perf_counter() - t0
+            line["train_loss"] = [float(losses[0]), float(losses[-1])]
+            model.attach(learned)
+            learned.set_option("order", 0 if args.no_learned_order else 1)
+            learned.set_option("h0", 1)
+            logs.clear()
+        if args.retrain_every and step > 6 and (step - 6) % args.retrain_every == 0 and logs:
+            t0 = time.perf_counter()
+            cat = [torch.cat([lg[k] for lg in logs]) for k in range(5)]
+            losses = model.train(*cat, epochs=20, batch=8192, lr=1e-3, seed=12 + step)
+            torch.cuda.synchronize()
+            line["train_s"] = time.perf_counter() - t0
+            line["train_loss"] = [float(losses[0]), float(losses[-1])]
+            model.attach(learned)
+            logs.clear()
+        T, Y, ms, s = timed(plain, T0, p, Y0)
+        line.update({"plain_ms": ms, "plain_substeps": int(s["substeps"].sum()),
+                     "plain_rejects": int(s["rejects"].sum()), "plain_failed": int((s["status"] != 0).sum())})
+        if step <= 5:
+            logs.append((T0, p, Y0, s["substeps"].clone(), s["h_first"].clone()))
+        else:
+            _, _, ms2, s2 = timed(learned, T0, p, Y0)
+            if args.retrain_every:
+                logs.append((T0, p, Y0, s2["substeps"].clone(), s2["h_first"].clone()))
+            line.update({"learned_ms": ms2, "learned_substeps": int(s2["substeps"].sum()),
+                         "learned_rejects": int(s2["rejects"].sum()),
+                         "learned_failed": int((s2["status"] != 0).sum()), "speedup": ms / ms2})
+            tot["plain_ms"] += ms
+            tot["learned_ms"] += ms2
+            tot["plain_sub"] += line["plain_substeps"]
+            tot["learned_sub"] += line["learned_substeps"]
+        print(json.dumps(line), flush=True)
+        st = synth.perturb_states(synth.CellStates(T=T.cpu().numpy(), p=st.p, Y=Y.cpu().numpy(), kind=st.kind),
+                                  seed=100 + step)
+    print(json.dumps({"cfd_loop_summary": "steps 6-20", "n_cells": n, "retrain_every": args.retrain_every,
+                      "learned_order": not args.no_learned_order,
+                      "plain_cells_step_per_s": 15 * n / (tot["plain_ms"] / 1e3),
+                      "learned_cells_step_per_s": 15 * n / (tot["learned_ms"] / 1e3),
+                      "speedup": tot["plain_ms"] / tot["learned_ms"],
+                      "substeps_ratio": tot["learned_sub"] / tot["plain_sub"]}), flush=True)
+
+
 def main():
     args = parse()
     if args.sweep:
         run_sweep(args)
+        return
+    if args.cfd_loop:
+        run_cfd_loop(args)
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

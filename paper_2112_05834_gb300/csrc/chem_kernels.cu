@@ -1460,9 +1460,13 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
     h_cp_mass(m, c, c.y[0], c.y + 1, h_target, cp_dummy);
     // initial step
     double h = -1.0;
+    bool guard = false;  // a supplied initial step, checked against f(y0) at the first step
     if (args.use_h0 && job.h0) {
       const double g = job.h0[cell];
-      if (isfinite(g) && g > 0.0) h = fmin(g, dt);
+      if (isfinite(g) && g > 0.0) {
+        h = fmin(g, dt);
+        guard = true;
+      }
     }
     if (h <= 0.0) {
       eval_rhs<NW, false, Policy<PREC>::IR>(m, c, c.y, p, c.f0);
@@ -1479,12 +1483,28 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
       ++steps;
       // Jacobian and f0 at y; iteration matrix; factorisation
       PHASE(1);
+      // A supplied initial step (learned or carried over) is kept inside the starting
+      // step heuristic's envelope [h_a, 100 h_a], h_a = 0.01 |y0| / |f(y0)| in the WRMS
+      // norm: f(y0) is the first step's first-stage RHS, so the check costs no RHS
+      // evaluation, and a prediction far from the states it was trained on cannot cost
+      // more than the heuristic's own range of answers.
+      auto apply_guard = [&]() {
+        if (!guard) return;
+        guard = false;
+        const double d0 = wrms(c, n, c.y, c.y, c.y, rtol, atol);
+        const double d1 = wrms(c, n, c.f0, c.y, c.y, rtol, atol);
+        const double ha = d1 > 1e-300 ? 0.01 * d0 / d1 : dt;
+        h = fmin(fmin(fmax(h, ha), 100.0 * ha), dt - t);
+        h_unclipped = h;
+      };
       if (PREC == PREC_FP64 && args.jac_fd) {
         eval_rhs<NW, false, false>(m, c, c.y, p, c.f0);
+        apply_guard();
         PHASE(2);
         fd_matrix<NW, false>(m, c, p, c.y, c.f0, 1.0 / (h * kRodasGamma));
       } else {
         const Scal s = eval_rhs<NW, true, Policy<PREC>::IR>(m, c, c.y, p, c.f0);
+        apply_guard();
         PHASE(2);
         build_matrix<NW, PREC, false>(m, c, s, c.f0, 1.0 / (h * kRodasGamma));
       }
