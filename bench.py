@@ -61,7 +61,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU baseline time budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--forms", default="plain_fp64,headline")
+    ap.add_argument("--forms", default="plain_fp64,mixed,headline",
+                    help="plain_fp64: FP64, one CTA per cell; mixed: mixed precision + work queue; "
+                         "headline: mixed + queue + learned order/h0")
     ap.add_argument("--sweep", action="store_true",
                     help="per-cell time vs absolute tolerance for the FP64 form's classical variants "
                          "(forward-difference Jacobian, elimination without pivoting); one JSON line each")
@@ -255,8 +257,9 @@ def run_ours(args, rank, world):
 
     forms = {}
     plain = pkg.Integrator(m, precision=0, scheduler=0)
+    mixed = pkg.Integrator(m, precision=1, scheduler=2, ir_sweeps=1)
     head = pkg.Integrator(m, precision=1, scheduler=2, ir_sweeps=1)
-    for integ in (plain, head):
+    for integ in (plain, mixed, head):
         integ.set_option("time_kernel", 1)  # CUDA events around the integration kernel
     learned = False
     if not args.no_learned and hasattr(pkg, "train_cost_model"):
@@ -264,6 +267,8 @@ def run_ours(args, rank, world):
     want = args.forms.split(",")
     if "plain_fp64" in want:
         forms["plain_fp64"] = plain
+    if "mixed" in want:
+        forms["mixed"] = mixed
     if "headline" in want:
         forms["headline"] = head
 
@@ -536,6 +541,14 @@ def main():
         if "phases" in pl:
             line["plain_fp64"]["phase_share"] = pl["phases"]
         line["speedup_vs_plain_fp64"] = value / pv
+    if "mixed" in res:
+        mx = res["mixed"]
+        mv = n * args.steps / (mx["ms_total"] / 1e3)
+        line["mixed_without_learned"] = {"value": mv, "ms_per_step": mx["ms_total"] / args.steps,
+                                         "kernel_ms": mx["kernel_ms"], "substeps_per_step": mx["substeps"]}
+        if "phases" in mx:
+            line["mixed_without_learned"]["phase_share"] = mx["phases"]
+        line["learned_gain"] = value / mv
     if "phases" in hd:
         line["phase_share"] = hd["phases"]
         line["phase_roofline"] = phase_rooflines(m, hd, n, mlp_ms)

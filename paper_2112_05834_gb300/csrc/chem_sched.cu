@@ -5,8 +5,10 @@
 // This replaces DLBFoam's MPI redistribution of cell problems (paper:
 // Methodology, "DLBFoam: Dynamic load balancing"): instead of moving problems
 // from busy to idle ranks, persistent CTAs pull cells from one device counter,
-// and the queue is ordered so the most expensive cells start first and the tail
-// of the launch is made of cheap cells.
+// and the queue starts with the most expensive tenth of the cells, heaviest
+// first, so no expensive cell is left for the tail of the launch; the rest keep
+// their index order (sorting them as well measured slower than leaving the
+// bulk of the batch mixed).
 
 #include <cuda_runtime.h>
 
@@ -52,8 +54,12 @@ __global__ void k_hist(const float* cost, int64_t n, int* hist) {
     if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
-__global__ void k_scan(int* hist) {
-  // single block of kBuckets threads: exclusive prefix sum in place
+// Heaviest share of the cells that is ordered by cost; the rest keeps index order.
+constexpr float kHeavyShare = 0.1f;
+
+__global__ void k_scan(int* hist, int64_t n) {
+  // single block of kBuckets threads: exclusive prefix sum in place; hist[kBuckets]
+  // receives the last bucket of the heavy share (its inclusive sum reaches the share)
   __shared__ int sh[kBuckets];
   const int t = threadIdx.x;
   sh[t] = hist[t];
@@ -65,18 +71,25 @@ __global__ void k_scan(int* hist) {
     __syncthreads();
   }
   hist[t] = t == 0 ? 0 : sh[t - 1];
+  const long long share = (long long)(kHeavyShare * (float)n) > 0 ? (long long)(kHeavyShare * (float)n) : 1;
+  const bool reach = sh[t] >= share, before = t > 0 && sh[t - 1] >= share;
+  if (reach && !before) hist[kBuckets] = t;
 }
 
 __global__ void k_scatter(const float* cost, int64_t n, int* offs, int* perm) {
+  const int last = offs[kBuckets];  // buckets after it form one index-ordered group
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int pos = atomicAdd(&offs[cost_bucket(cost[i])], 1);
+    int b = cost_bucket(cost[i]);
+    if (b > last) b = last + 1;
+    const int pos = atomicAdd(&offs[b], 1);
     perm[pos] = (int)i;
   }
 }
 
 }  // namespace
 
-// perm[0..n) = cell indices ordered by decreasing cost (ties in arbitrary order).
+// perm[0..n): the heaviest tenth of the cells by decreasing cost, then the others
+// (order within a cost bucket and within the others set by the scatter's atomics).
 chem_status chem_internal_cost_order(chem_handle h, const float* d_cost, int64_t n, cudaStream_t st,
                                      const int** perm_out) {
   if (n > h->order_cap) {
@@ -87,16 +100,16 @@ chem_status chem_internal_cost_order(chem_handle h, const float* d_cost, int64_t
       cudaFree(h->d_order);
       h->d_order = nullptr;
     }
-    chem_status s = chem_internal_alloc(h, &h->d_order, (size_t)n * 4 + kBuckets * 4);
+    chem_status s = chem_internal_alloc(h, &h->d_order, (size_t)n * 4 + (kBuckets + 1) * 4);
     if (s != CHEM_OK) return s;
     h->order_cap = n;
   }
   int* perm = static_cast<int*>(h->d_order);
   int* hist = perm + h->order_cap;
-  cudaMemsetAsync(hist, 0, kBuckets * 4, st);
+  cudaMemsetAsync(hist, 0, (kBuckets + 1) * 4, st);
   const int grid = (int)std::min<int64_t>((n + 255) / 256, 4 * (int64_t)h->num_sms);
   k_hist<<<grid, 256, 0, st>>>(d_cost, n, hist);
-  k_scan<<<1, kBuckets, 0, st>>>(hist);
+  k_scan<<<1, kBuckets, 0, st>>>(hist, n);
   k_scatter<<<grid, 256, 0, st>>>(d_cost, n, hist, perm);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
