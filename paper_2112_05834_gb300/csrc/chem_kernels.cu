@@ -1,11 +1,15 @@
 // Device code of the batched stiff-chemistry integrator (sm_103a).
 //
 // One CTA integrates one cell at a time; its warps share the cell's work:
-// species and reactions are strided over threads for the rates, Jacobian rows
-// and columns over warps/lanes for the assembly, rows over warps for the LU
-// trailing update, and one warp runs the triangular solves. All per-cell data
-// (state, stage vectors, per-reaction derivative data, the iteration matrix)
-// lives in shared memory; the mechanism tables are read through the L1 cache.
+// species and 32-reaction chunks are dealt over threads and warps for the rates,
+// Jacobian rows over warps (columns over lanes) for the assembly; the FP64 form
+// factorises in shared memory (rows over warps) and solves on one warp, the mixed
+// form inverts in FP32 with the matrix in registers (columns over warps, rows over
+// lanes) and solves by matrix-vector products over all threads. All per-cell data
+// (state, stage vectors, per-reaction derivative data, the iteration matrix) lives
+// in shared memory, except that the mixed form may keep its FP64 assembled matrix
+// in a global-memory slot of the CTA when that lets more CTAs share an SM; the
+// mechanism tables are read through the L1 cache.
 //
 // Paper mapping: rates and RHS = pyJac's reaction-rate evaluation; analytic
 // Jacobian = pyJac's Jacobian (Methodology, "Analytical Jacobian and improved ODE
@@ -1351,7 +1355,7 @@ __device__ void fd_matrix(const DevMech& m, Cta<NW>& c, double p, const double* 
 }
 
 // WRMS norm of e with scale atol + rtol max(|ya|, |yb|). With step_fac, also the
-// step-size factor 0.9 err^(-1/4) (kFacMax for err = 0); both come from warp 0.
+// step-size factor 0.9 err^(-1/4) (kFacMax for err = 0); both come from the CTA's last warp.
 template <int NW>
 __device__ double wrms(Cta<NW>& c, int n, const double* e, const double* ya, const double* yb,
                        double rtol, double atol, double* step_fac = nullptr) {
@@ -1605,12 +1609,13 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
-// Launch bounds keep 128 registers a thread: four CTAs of 128 threads, eight of 64 or
-// two of 256 fill the register file. Four CTAs of 128 threads also match what the
-// shared-memory footprint allows for mechanisms up to ~60 species; the larger counts
-// need the global-memory slot for the mixed form's FP64 matrix.
+// Launch bounds: 128 registers a thread for four CTAs of 128 threads (FP64 form: its
+// shared-memory footprint allows no more up to ~60 species), eight of 64 or two of 256;
+// the mixed form with 128 threads takes 96 registers for five CTAs per SM, which its
+// global-memory matrix slot makes room for (measured on 54 species: 7 % faster than
+// four CTAs; six and seven CTAs spill too much in the register Gauss-Jordan).
 template <int NW, int PREC>
-__global__ void __launch_bounds__(NW * 32, NW == 4 ? 4 : NW == 2 ? 8 : 2) k_integrate(const __grid_constant__ IntegrateArgs args) {
+__global__ void __launch_bounds__(NW * 32, NW == 4 ? (PREC == PREC_MIXED ? 5 : 4) : NW == 2 ? 8 : 2) k_integrate(const __grid_constant__ IntegrateArgs args) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long s_work;
   const bool m0g = PREC == PREC_MIXED && args.m0_scratch != nullptr;
