@@ -1163,20 +1163,32 @@ __device__ int gj_invert_wc(Cta<NW>& c, float* A, int n) {
 #pragma unroll
         for (int s = 0; s < RS; ++s) v[s] = a[s][cc];
       }
-    float bv = -1.0f, bval = 0.0f;
-    int bi = n;
+    // argmax of |a_ik| over the unused rows, lowest row on ties, NaN never chosen: the
+    // bit pattern of a non-negative float orders like its value, so key = bits + 1
+    // (0: no candidate) goes through one warp max-reduction; the first row slot, then
+    // the lowest lane, holding the maximum is the lowest row index that has it
+    unsigned key[RS];
+    unsigned kmax = 0u;
 #pragma unroll
     for (int s = 0; s < RS; ++s) {
       const int i = lane + 32 * s;
       const float x = fabsf(v[s]);
-      if (i < n && !((used >> s) & 1u) && (x > bv || (x == bv && i < bi))) { bv = x; bi = i; bval = v[s]; }
+      key[s] = (i < n && !((used >> s) & 1u) && !isnan(x)) ? __float_as_uint(x) + 1u : 0u;
+      kmax = max(kmax, key[s]);
     }
+    const unsigned km = __reduce_max_sync(FULLMASK, kmax);
+    int bi = n;
+    float bval = 0.0f;
+    if (km != 0u) {
 #pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      const float ov = __shfl_xor_sync(FULLMASK, bv, o);
-      const int oi = __shfl_xor_sync(FULLMASK, bi, o);
-      const float ox = __shfl_xor_sync(FULLMASK, bval, o);
-      if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; bval = ox; }
+      for (int s = 0; s < RS; ++s) {
+        const unsigned b = __ballot_sync(FULLMASK, key[s] == km);
+        if (bi == n && b != 0u) {
+          const int l = __ffs(b) - 1;
+          bi = l + 32 * s;
+          bval = __shfl_sync(FULLMASK, v[s], l);
+        }
+      }
     }
 #pragma unroll
     for (int s = 0; s < RS; ++s)
