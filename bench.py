@@ -75,6 +75,10 @@ def parse():
                          "of the last N steps (0: train once, on steps 1-5)")
     ap.add_argument("--no-learned-order", action="store_true",
                     help="with --cfd-loop: learned initial step only, index order")
+    ap.add_argument("--refmap", action="store_true",
+                    help="reference mapping by mixture fraction: the mixed form on the 54-species workload "
+                         "with a 40 %% oxidiser zone (c54_65k_oxzone unless --workload names another), "
+                         "without and with mapping; one JSON line each")
     ap.add_argument("--no-phases", action="store_true",
                     help="skip the extra untimed step per form with per-phase cycle counters")
     return ap.parse_args()
@@ -380,6 +384,50 @@ def run_sweep(args):
             integ.close()
 
 
+def run_refmap(args):
+    """Whole-call device time of chem_integrate (CUDA events on the stream, mapping
+    kernels included) without and with reference mapping, mixed form, work queue.
+    Each variant: one warm-up and three timed calls from the same initial state
+    (restored by a device copy outside the timed region); the median is reported."""
+    import torch
+
+    import paper_2112_05834_gb300 as pkg
+
+    wl = "c54_65k_oxzone" if args.workload == "c54_65k" else args.workload
+    m, st, dt = synth.workload(wl, n_cells=args.cells)
+    n = st.T.shape[0]
+    yf, yo = synth.streams(m)
+    dev = torch.device("cuda", 0)
+    T0, p, Y0 = (torch.tensor(a, device=dev) for a in (st.T, st.p, st.Y))
+    stream = torch.cuda.current_stream()
+    variants = [("no_mapping", None), ("mapping_Ztol1e-4_Ttol2K", (1e-4, 2.0)),
+                ("mapping_Ztol1e-4_Ttol10K", (1e-4, 10.0))]
+    for name, zt in variants:
+        integ = pkg.Integrator(m, precision=1, scheduler=2, time_kernel=1)
+        if zt is not None:
+            integ.set_reference_mapping(yf, yo, 0.0, zt[0], zt[1])
+        times, kms = [], []
+        for rep in range(4):
+            T, Y = T0.clone(), Y0.clone()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            integ.integrate(T, p, Y, dt, 1e-8, 1e-12)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep > 0:
+                times.append(e0.elapsed_time(e1))
+                kms.append(integ.kernel_ms())
+        tot = integ.totals()
+        nm = integ.reference_mapping(n)[1] if zt is not None else 0
+        ms = float(np.median(times))
+        print(json.dumps({"refmap": name, "workload": wl, "n_cells": n, "rtol": 1e-8, "atol": 1e-12,
+                          "cells_per_s": n / (ms * 1e-3), "call_ms": ms,
+                          "integration_kernel_ms": float(np.median(kms)), "n_mapped": nm,
+                          "substeps": tot["substeps"], "failed": tot["failed"]}), flush=True)
+        integ.close()
+
+
 def run_cfd_loop(args):
     """Learned scheduling + initial step at scale: the 100-species mechanism, 1,048,576
     cells (or --cells), 20 CFD steps of dt with the seeded mixing perturbation between
@@ -469,6 +517,9 @@ def main():
         return
     if args.cfd_loop:
         run_cfd_loop(args)
+        return
+    if args.refmap:
+        run_refmap(args)
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -254,6 +254,66 @@ chem_status chem_get_phase_cycles(chem_handle h, void* stream, uint64_t* cycles,
  */
 chem_status chem_get_kernel_ms(chem_handle h, float* ms);
 
+/* ------------------------------------------------------------------------
+ * Reference mapping by mixture fraction (paper: Methodology, "DLBFoam: Dynamic
+ * load balancing": cells are either integrated or mapped from a reference
+ * solution with a similar Bilger mixture fraction Z).
+ *
+ * Bilger's coupling function beta = 2 Z_C/W_C + Z_H/(2 W_H) - Z_O/W_O of the
+ * element mass fractions is, per cell, beta = sum_k b_k Y_k with
+ * b_k = (2 a_Ck + a_Hk/2 - a_Ok) / W_k (a_ek: the mechanism's atom counts), and
+ * Z = (beta - beta_ox) / (beta_fuel - beta_ox).
+ *
+ * With mapping on, each chem_integrate call (one job, scheduler 2):
+ *   - zone: cells with |Z - Z_center| <= Z_tol (Z of the initial state);
+ *   - reference: the zone cell with the lowest index; it is integrated;
+ *   - mapped: every other zone cell with |T - T_ref| <= T_tol (initial T); it
+ *     is not integrated but receives the reference's change over the step,
+ *     T += T_ref(dt) - T_ref(0), Y_k += Y_ref,k(dt) - Y_ref,k(0). Its statistics
+ *     read 0 substeps, 0 rejections, h_first 0 and the reference's status; if the
+ *     reference failed, the mapped cells keep their initial state;
+ *   - every other cell is integrated as without mapping.
+ * Everything runs on the device on the call's stream (a few small kernels
+ * before and one after the integration kernel); the mapped cells are moved to
+ * the front of the work order and the work queue starts past them.
+ * ------------------------------------------------------------------------ */
+
+/*
+ * Defines the fuel and oxidiser streams and switches mapping on.
+ *   elem_C, elem_H, elem_O  columns of the mechanism's element table (desc.elem)
+ *                           holding carbon, hydrogen and oxygen atoms; -1 for an
+ *                           element the mechanism lacks (at least one >= 0)
+ *   Y_fuel[K], Y_ox[K]      host: mass fractions of the two streams (copied)
+ *   Z_center, Z_tol, T_tol  the zone and the temperature tolerance (K)
+ * Z_tol < 0 switches mapping off (the streams stay defined for
+ * chem_eval_mixture_fraction). Synchronous (uploads K coefficients). Errors:
+ * CHEM_ERR_INVALID_ARG for a column out of range, NULL or non-finite streams,
+ * equal beta of the two streams, NaN Z_tol, non-finite Z_center / T_tol or
+ * T_tol < 0. chem_integrate returns CHEM_ERR_INVALID_ARG while mapping is on
+ * for several jobs or a scheduler other than 2; chem_integrate_noalloc refuses
+ * a handle with mapping on.
+ */
+chem_status chem_set_reference_mapping(chem_handle h, int32_t elem_C, int32_t elem_H, int32_t elem_O,
+                                       const double* Y_fuel, const double* Y_ox, double Z_center,
+                                       double Z_tol, double T_tol);
+
+/*
+ * Z[n_cells] (device) = Bilger mixture fraction of the cells Y[n_cells][K]
+ * (device) for the streams of chem_set_reference_mapping. Stream-ordered.
+ * Errors: CHEM_ERR_INVALID_ARG (no streams defined, n_cells < 0, NULL arrays).
+ */
+chem_status chem_eval_mixture_fraction(chem_handle h, int64_t n_cells, const double* Y, double* Z,
+                                       void* stream);
+
+/*
+ * Outcome of the handle's last integration with mapping on: mapped[n] (DEVICE,
+ * may be NULL; 1 = mapped) and, on the host, the number of mapped cells and the
+ * reference cell's index (-1: empty zone). Synchronises `stream`. Returns
+ * CHEM_ERR_INVALID_ARG when the last integration ran without mapping.
+ */
+chem_status chem_get_reference_mapping(chem_handle h, void* stream, int32_t* mapped, int64_t* n_mapped,
+                                       int64_t* ref_cell);
+
 /* Last error message of the handle (or of the last chem_create when h is NULL). */
 const char* chem_last_error(chem_handle h);
 

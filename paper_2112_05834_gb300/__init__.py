@@ -42,6 +42,9 @@ SIGNATURES = {
     "chem_lu_solve_batched": (C.c_int, [_I64, _I32, _P, _P, _P, _P, _I32, _I32, _P]),
     "chem_eval_math": (C.c_int, [_I32, _I64, _P, _P, _P]),
     "chem_get_kernel_ms": (C.c_int, [_P, _P]),
+    "chem_set_reference_mapping": (C.c_int, [_P, _I32, _I32, _I32, _P, _P, _D, _D, _D]),
+    "chem_eval_mixture_fraction": (C.c_int, [_P, _I64, _P, _P, _P]),
+    "chem_get_reference_mapping": (C.c_int, [_P, _P, _P, _P, _P]),
     "chem_rosenbrock_tableau": (None, [_P, _P, _P, _P, _P]),
     "chem_get_phase_cycles": (C.c_int, [_P, _P, _P, _I32]),
     "chem_mlp_create": (C.c_int, [_I32, C.c_uint64, _P]),
@@ -141,6 +144,7 @@ class Integrator:
         h = C.c_void_p()
         _check(lib.chem_create(C.byref(d), C.byref(h)), None)
         self.h = h
+        self._elements = list(getattr(mech, "elements", []))
         self.K = mech.n_species
         self.I = mech.n_reactions
         self.n = self.K + 1
@@ -219,6 +223,41 @@ class Integrator:
         ms = C.c_float()
         _check(load().chem_get_kernel_ms(self.h, C.byref(ms)), self.h)
         return float(ms.value)
+
+    def set_reference_mapping(self, Y_fuel, Y_ox, Z_center=0.0, Z_tol=1e-4, T_tol=2.0):
+        """Reference mapping by Bilger mixture fraction (chem_set_reference_mapping);
+        Y_fuel / Y_ox are the streams' mass fractions [K]. Z_tol < 0 switches it off."""
+        col = {e: (self._elements.index(e) if e in self._elements else -1) for e in ("C", "H", "O")}
+        yf = np.ascontiguousarray(Y_fuel, dtype=np.float64)
+        yo = np.ascontiguousarray(Y_ox, dtype=np.float64)
+        if yf.shape != (self.K,) or yo.shape != (self.K,):
+            raise ValueError(f"stream compositions must have shape ({self.K},)")
+        _check(load().chem_set_reference_mapping(self.h, col["C"], col["H"], col["O"],
+                                                 yf.ctypes.data_as(C.c_void_p),
+                                                 yo.ctypes.data_as(C.c_void_p), float(Z_center),
+                                                 float(Z_tol), float(T_tol)), self.h)
+
+    def mixture_fraction(self, Y, stream=None):
+        """Bilger Z[n] of device Y[n, K] for the streams of set_reference_mapping."""
+        import torch
+
+        if not (isinstance(Y, torch.Tensor) and Y.is_cuda and Y.dtype == torch.float64
+                and Y.is_contiguous() and Y.dim() == 2 and Y.shape[1] == self.K):
+            raise TypeError(f"Y must be a contiguous CUDA float64 tensor [n, {self.K}]")
+        Z = torch.empty(Y.shape[0], dtype=torch.float64, device=Y.device)
+        _check(load().chem_eval_mixture_fraction(self.h, Y.shape[0], _dptr(Y), _dptr(Z),
+                                                 _stream_ptr(stream)), self.h)
+        return Z
+
+    def reference_mapping(self, n, stream=None):
+        """(mapped[n] int32 CUDA tensor, n_mapped, reference cell or -1) of the last call."""
+        import torch
+
+        mapped = torch.empty(n, dtype=torch.int32, device="cuda")
+        nm, ref = C.c_int64(), C.c_int64()
+        _check(load().chem_get_reference_mapping(self.h, _stream_ptr(stream), _dptr(mapped),
+                                                 C.byref(nm), C.byref(ref)), self.h)
+        return mapped, nm.value, ref.value
 
     def eval_rhs(self, T, p, Y, stream=None):
         import torch

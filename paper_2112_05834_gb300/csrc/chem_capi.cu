@@ -476,6 +476,10 @@ extern "C" chem_status chem_create(const chem_mechanism_desc* desc, chem_handle*
     delete h;
     return CHEM_ERR_CUDA;
   }
+  h->n_elem = desc->n_elements;
+  if (desc->n_elements > 0)
+    h->elem_host.assign(desc->elem, desc->elem + (size_t)desc->n_species * desc->n_elements);
+  h->W_host.assign(desc->W, desc->W + desc->n_species);
   chem_status s = build_tables(h, desc);
   if (s == CHEM_OK) s = chem_internal_alloc(h, &h->d_queue, sizeof(int) * 4);
   if (s != CHEM_OK) {
@@ -621,6 +625,15 @@ static bool bad_tol(double dt, double rtol, double atol) {
 chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double dt, double rtol,
                                     double atol, cudaStream_t st) {
   chem_handle h0 = jobs[0].h;
+  bool rm = false;  // reference mapping (one job, queue scheduler)
+  for (int j = 0; j < n_jobs; ++j) {
+    rm = rm || jobs[j].h->refmap;
+    jobs[j].h->rm_last_n = -1;
+  }
+  if (rm && (n_jobs != 1 || h0->scheduler != SCHED_QUEUE)) {
+    h0->err = "chem_integrate: reference mapping needs one job and the queue scheduler";
+    return CHEM_ERR_INVALID_ARG;
+  }
   IntegrateArgs a;
   std::memset(&a, 0, sizeof a);
   int64_t total = 0;
@@ -737,8 +750,19 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
       a.m0_stride = stride;
     }
   }
+  // reference mapping: mapped cells go to the front of the work order and the
+  // queue starts past them; after the launch they take the reference's change
+  if (rm) {
+    s = chem_internal_refmap_prepare(h0, jobs[0], &a, st);
+    if (s != CHEM_OK) return s;
+  }
   s = chem_internal_launch(h0, a, block, grid, st);
+  h0->queue_preset = false;
   if (s != CHEM_OK) return s;
+  if (rm) {
+    s = chem_internal_refmap_apply(h0, jobs[0], st);
+    if (s != CHEM_OK) return s;
+  }
   for (int j = 0; j < n_jobs; ++j) {
     jobs[j].h->cost_valid = true;
     jobs[j].h->cost_n = jobs[j].n_cells;
@@ -781,7 +805,7 @@ chem_status chem_internal_launch(chem_handle h, const IntegrateArgs& a, int bloc
     chem_status s = chem_internal_graph_launch(h, a, block, grid, st);
     if (s != CHEM_OK) return s;
   } else {
-    if (a.sched == SCHED_QUEUE) CHEM_CUDA(h, cudaMemsetAsync(a.queue, 0, sizeof(int), st));
+    if (a.sched == SCHED_QUEUE && !h->queue_preset) CHEM_CUDA(h, cudaMemsetAsync(a.queue, 0, sizeof(int), st));
     if (h->time_kernel) CHEM_CUDA(h, cudaEventRecord(h->kev0, st));
     CHEM_CUDA(h, launch_integrate(a, block, h->precision, grid, st));
   }

@@ -69,6 +69,22 @@ struct chem_handle_s {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::vector<unsigned char> gkey;
+  // reference mapping by mixture fraction (chem_set_reference_mapping)
+  std::vector<int> elem_host;     // [K][n_elem] atom counts kept from chem_create
+  std::vector<double> W_host;     // [K] molar masses
+  int n_elem = 0;
+  bool rm_streams = false;        // fuel / oxidiser streams defined
+  bool refmap = false;            // mapping on
+  double rm_beta_o = 0.0, rm_dbeta = 1.0;  // beta of the oxidiser; beta_fuel - beta_ox
+  double rm_Zc = 0.0, rm_Ztol = -1.0, rm_Ttol = 0.0;
+  double* d_rm_b = nullptr;       // [K] Bilger coefficients b_k
+  void* d_rm_misc = nullptr;      // reference index, info[2] (mapped count, reference), ref0[K+1]
+  void* d_rm_flag = nullptr;      // [cap] int32: zone flags, then mapped flags
+  void* d_rm_perm = nullptr;      // [cap] int32: partitioned work order
+  void* d_rm_tiles = nullptr;     // [cap / 1024] tile counts / offsets
+  int64_t rm_cap = 0;
+  int64_t rm_last_n = -1;         // cells of the last mapped call (-1: last call unmapped)
+  bool queue_preset = false;      // the next launch keeps the queue's start (set by the mapping)
   // autotuner cache: key -> block
   long long autotuned_key = -1;
   int autotuned_block = 128;
@@ -87,3 +103,6 @@ chem_status chem_internal_autotune(chem_handle h, const chem::IntegrateArgs& a, 
 chem_status chem_internal_prepare_learned(chem_handle h, const chem_job* jobs, int32_t n_jobs,
                                           chem::IntegrateArgs* a, cudaStream_t st);
 void chem_internal_release_learned(chem_handle h);
+chem_status chem_internal_refmap_prepare(chem_handle h, const chem_job& job, chem::IntegrateArgs* a,
+                                         cudaStream_t st);
+chem_status chem_internal_refmap_apply(chem_handle h, const chem_job& job, cudaStream_t st);

@@ -83,6 +83,10 @@ extern "C" chem_status chem_integrate_noalloc(chem_handle h, int64_t n_cells, do
              CHEM_STR(CHEM_NOALLOC_MAX_CELLS) " cells; split the batch or use chem_integrate";
     return CHEM_ERR_INVALID_ARG;
   }
+  if (h->refmap) {
+    h->err = "chem_integrate_noalloc: reference mapping needs handle-owned buffers; use chem_integrate";
+    return CHEM_ERR_INVALID_ARG;
+  }
   if (n_cells == 0) return CHEM_OK;
   unsigned char* base = nullptr;
   chem_status s = scratch_address(h, &base);

@@ -170,9 +170,9 @@ chem_status chem_internal_prepare_learned(chem_handle h, const chem_job* jobs, i
 // ---------------------------------------------------------------------------
 chem_status chem_internal_graph_launch(chem_handle h, const IntegrateArgs& a, int block, int grid,
                                        cudaStream_t st) {
-  std::vector<unsigned char> key(sizeof(IntegrateArgs) + 3 * sizeof(int));
+  std::vector<unsigned char> key(sizeof(IntegrateArgs) + 4 * sizeof(int));
   std::memcpy(key.data(), &a, sizeof(IntegrateArgs));
-  int extra[3] = {block, grid, h->precision};
+  int extra[4] = {block, grid, h->precision, h->queue_preset ? 1 : 0};
   std::memcpy(key.data() + sizeof(IntegrateArgs), extra, sizeof extra);
   if (!h->gexec || key != h->gkey) {
     if (h->gexec) {
@@ -190,7 +190,8 @@ chem_status chem_internal_graph_launch(chem_handle h, const IntegrateArgs& a, in
     occupancy_integrate(block, h->precision, a.smem_K, a.smem_I, &occ, a.m0_scratch != nullptr);  // sets kernel attributes
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess && a.sched == SCHED_QUEUE) e = cudaMemsetAsync(a.queue, 0, sizeof(int), h->cap_stream);
+    if (e == cudaSuccess && a.sched == SCHED_QUEUE && !h->queue_preset)
+      e = cudaMemsetAsync(a.queue, 0, sizeof(int), h->cap_stream);
     if (e == cudaSuccess) e = launch_integrate(a, block, h->precision, grid, h->cap_stream);
     cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
     if (e == cudaSuccess) e = e2;

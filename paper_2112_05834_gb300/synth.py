@@ -379,6 +379,18 @@ def unreacted_mixture(mech: Mechanism, ratio, x_inert=0.7):
     return _mole_to_mass(X, mech.W)
 
 
+def streams(mech: Mechanism, x_inert=0.7):
+    """(Y_fuel, Y_ox): the pure fuel stream and the oxidiser stream O2/N2 with
+    X_N2 = x_inert (the two streams whose mixing the mixture fraction measures)."""
+    K = mech.n_species
+    Xf = np.zeros(K)
+    Xf[mech.roles["fuel"]] = 1.0
+    Xo = np.zeros(K)
+    Xo[mech.roles["inert"]] = x_inert
+    Xo[mech.roles["oxidizer"]] = 1.0 - x_inert
+    return _mole_to_mass(Xf, mech.W), _mole_to_mass(Xo, mech.W)
+
+
 def burnt_products(mech: Mechanism, Y):
     """Complete-combustion products of mixtures Y (atom bookkeeping only).
 
@@ -424,7 +436,7 @@ class CellStates:
     T: np.ndarray   # [N] K
     p: np.ndarray   # [N] dyn/cm^2
     Y: np.ndarray   # [N, K] mass fractions
-    kind: np.ndarray  # [N] int8: 0 unreacted/cold, 1 igniting, 2 burnt
+    kind: np.ndarray  # [N] int8: 0 unreacted/cold, 1 igniting, 2 burnt, 3 oxidiser
 
 
 def gen_states(mech: Mechanism, n_cells: int, seed: int = 1, p: float = ATM,
@@ -437,12 +449,14 @@ def gen_states(mech: Mechanism, n_cells: int, seed: int = 1, p: float = ATM,
     unreacted = fuel/O2/N2 with X_fuel/X_O2 ~ U(ratio_range) and X_N2 = x_inert;
     burnt = complete-combustion products blended with the unreacted mixture
     at a weight <= 1e-3; igniting = convex blend (1-c) unreacted + c burnt with
-    c ~ U[0.1, 0.9]. Blends are in mass fractions, so element mass fractions
-    equal those of the unreacted mixture. Cells are shuffled (seeded) so cost is
+    c ~ U[0.1, 0.9]; oxidiser = the oxidiser stream of ``streams`` blended with
+    the unreacted mixture at a weight <= 1e-4 (the air side of a mixing layer,
+    mixture fraction near 0). Blends are in mass fractions, so element mass
+    fractions are those of the blended inputs. Cells are shuffled (seeded) so cost is
     spatially mixed, as in a decomposed CFD domain.
     """
     rng = np.random.default_rng(seed)
-    kinds = {"unreacted": 0, "igniting": 1, "burnt": 2}
+    kinds = {"unreacted": 0, "igniting": 1, "burnt": 2, "oxidiser": 3}
     fr = np.array([c[0] for c in classes], dtype=np.float64)
     counts = np.floor(fr / fr.sum() * n_cells).astype(np.int64)
     counts[0] += n_cells - counts.sum()
@@ -454,6 +468,9 @@ def gen_states(mech: Mechanism, n_cells: int, seed: int = 1, p: float = ATM,
         Yu = unreacted_mixture(mech, ratio, x_inert)
         if kind == "unreacted":
             Y = Yu
+        elif kind == "oxidiser":
+            w = rng.uniform(0.0, 1e-4, size=(m, 1))
+            Y = (1.0 - w) * streams(mech, x_inert)[1] + w * Yu
         else:
             Yb = burnt_products(mech, Yu)
             if kind == "burnt":
@@ -480,6 +497,10 @@ def gen_states(mech: Mechanism, n_cells: int, seed: int = 1, p: float = ATM,
 MIXED_CLASSES = ((0.6, "unreacted", 700.0, 900.0), (0.3, "igniting", 1000.0, 1600.0),
                  (0.1, "burnt", 2000.0, 2700.0))
 
+# the mixed classes beside an oxidiser zone of 40 % of the cells at 800 +- 5 K
+OXZONE_CLASSES = ((0.4, "oxidiser", 795.0, 805.0), (0.36, "unreacted", 700.0, 900.0),
+                  (0.18, "igniting", 1000.0, 1600.0), (0.06, "burnt", 2000.0, 2700.0))
+
 
 def perturb_states(states: CellStates, seed: int, dT: float = 50.0, w_max: float = 0.1):
     """Mixing perturbation between CFD steps: T += U[-dT, dT];
@@ -503,6 +524,7 @@ WORKLOADS = {
     "h2_10_1k": ("h2_10", 1024, ATM, ((1.0, "unreacted", 1000.0, 1800.0),), 1e-5),
     "c54_65k": ("c_54", 65536, 60 * BAR, MIXED_CLASSES, 1e-6),
     "c54_262k": ("c_54", 262144, 60 * BAR, MIXED_CLASSES, 1e-6),
+    "c54_65k_oxzone": ("c_54", 65536, 60 * BAR, OXZONE_CLASSES, 1e-6),
     "c100_262k": ("c_100", 262144, 40 * BAR, MIXED_CLASSES, 1e-6),
     "c100_1m": ("c_100", 1048576, 40 * BAR, MIXED_CLASSES, 1e-6),
 }
