@@ -210,3 +210,32 @@ def test_refmap_full_size(pkg, rm):
     j = int(np.flatnonzero(sample == r)[0])
     _bound(g["T"][mp], g["Y"][mp], st.T[mp] + (o["T"][j] - st.T[r]), st.Y[mp] + (o["Y"][j] - st.Y[r]),
            "sampled mapped cells")
+
+
+def test_refmap_many_tiles(pkg, rm):
+    """1,100,000 hydrogen-mechanism cells (no carbon column): 1,075 partition tiles, so
+    the tile-offset scan runs in two chunks of 1,024, and a ragged last tile. Every
+    integrated cell is integrated once, every mapped cell is not, the selection equals
+    the oracle's and the mapped cells carry the reference's change bit for bit."""
+    m = synth.mechanism_preset("h2_10")
+    n = 1_100_000
+    st = synth.gen_states(m, n, seed=11, p=synth.ATM,
+                          classes=((0.9, "oxidiser", 795.0, 805.0), (0.1, "unreacted", 700.0, 900.0)))
+    yf, yo = synth.streams(m)
+    Z = rm.mixture_fraction(m, st.Y, yf, yo)
+    zone, r, mapped = rm.select(Z, st.T, 0.0, ZTOL, 10.0)
+    near = _near_boundary(Z, st.T, r, 0.0, ZTOL, 10.0)
+    integ = pkg.Integrator(m, precision=1)
+    integ.set_reference_mapping(yf, yo, 0.0, ZTOL, 10.0)
+    T, p, Y = _dev(st.T), _dev(st.p), _dev(st.Y)
+    integ.integrate(T, p, Y, 1e-5, RTOL, ATOL)
+    g_mapped, nm, ref = integ.reference_mapping(n)
+    g_mapped = g_mapped.cpu().numpy().astype(bool)
+    assert ref == r
+    assert np.array_equal(g_mapped[~near], mapped[~near])
+    assert nm == int(g_mapped.sum()) > n // 2
+    sub = integ.stats(n)["substeps"].cpu().numpy()
+    assert np.all(sub[g_mapped] == 0) and np.all(sub[~g_mapped] > 0)
+    Tg, Yg = T.cpu().numpy(), Y.cpu().numpy()
+    np.testing.assert_array_equal(Tg[g_mapped], st.T[g_mapped] + (Tg[r] - st.T[r]))
+    np.testing.assert_array_equal(Yg[g_mapped], st.Y[g_mapped] + (Yg[r] - st.Y[r]))
