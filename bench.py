@@ -79,6 +79,10 @@ def parse():
                     help="reference mapping by mixture fraction: the mixed form on the 54-species workload "
                          "with a 40 %% oxidiser zone (c54_65k_oxzone unless --workload names another), "
                          "without and with mapping; one JSON line each")
+    ap.add_argument("--batching", action="store_true",
+                    help="the batching configuration, FP64 throughout: 262,144 cells of the 54-species "
+                         "workload, plain launch vs work queue + autotuner + CUDA graph; then four "
+                         "mechanisms (10, 32, 54, 100 species) in one launch vs four launches")
     ap.add_argument("--no-phases", action="store_true",
                     help="skip the extra untimed step per form with per-phase cycle counters")
     return ap.parse_args()
@@ -428,6 +432,83 @@ def run_refmap(args):
         integ.close()
 
 
+def run_batching(args):
+    """FP64 throughout. (1) 262,144 cells of the 54-species workload: one CTA per cell
+    (the plain launch) against persistent CTAs on the device work queue with the block
+    size from the autotuner and the launch captured in a CUDA graph. (2) Four mechanisms
+    (10, 32, 54, 100 species; a quarter of the cells each, same cell mix at 60 bar) in one
+    launch against four launches in sequence and four concurrent launches (option
+    job_launch). CUDA events on the stream around each call; one
+    warm-up call (for the batching form it includes the autotuner's trials and the graph
+    capture, timed separately) and two timed calls from the same initial state."""
+    import torch
+
+    import paper_2112_05834_gb300 as pkg
+
+    n = args.cells or 262144
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda", 0)
+
+    def timed(call, inputs, reps=2):
+        out = []
+        for r in range(1 + reps):
+            arrs = [tuple(t.clone() for t in x) for x in inputs]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            call(arrs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return out[0], float(np.median(out[1:]))
+
+    m, st, dt = synth.workload("c54_262k", n_cells=n)
+    x = [tuple(torch.tensor(a, device=dev) for a in (st.T, st.p, st.Y))]
+    res = {}
+    for name, opt in (("plain_launch", dict(precision=0, scheduler=0)),
+                      ("queue_autotune_graph", dict(precision=0, scheduler=2, autotune=1, graph=1))):
+        integ = pkg.Integrator(m, **opt)
+        first, ms = timed(lambda a, i=integ: i.integrate(a[0][0], a[0][1], a[0][2], dt, 1e-8, 1e-12), x)
+        tot = integ.totals()
+        res[name] = ms
+        print(json.dumps({"batching": name, "workload": "c54_262k", "n_cells": n, "dtype": "f64",
+                          "cells_per_s": n / (ms * 1e-3), "call_ms": ms, "first_call_ms": first,
+                          "block": int(integ.get_option("last_block")), "substeps": tot["substeps"],
+                          "failed": tot["failed"]}), flush=True)
+        integ.close()
+    print(json.dumps({"batching": "speedup_queue_autotune_graph_over_plain",
+                      "value": res["plain_launch"] / res["queue_autotune_graph"]}), flush=True)
+
+    presets = ("h2_10", "c_32", "c_54", "c_100")
+    per = n // len(presets)
+    integs, inputs = [], []
+    for i, name in enumerate(presets):
+        mech = synth.mechanism_preset(name)
+        s = synth.gen_states(mech, per, seed=1 + i, p=60 * synth.BAR, classes=synth.MIXED_CLASSES)
+        integs.append(pkg.Integrator(mech, precision=0, scheduler=2))
+        inputs.append(tuple(torch.tensor(a, device=dev) for a in (s.T, s.p, s.Y)))
+
+    def joint(a):
+        pkg.integrate_jobs([(g, *t) for g, t in zip(integs, a)], dt, 1e-8, 1e-12)
+
+    def separate(a):
+        for g, t in zip(integs, a):
+            g.integrate(*t, dt, 1e-8, 1e-12)
+
+    def concurrent(a):
+        integs[0].set_option("job_launch", 1)
+        joint(a)
+        integs[0].set_option("job_launch", 0)
+
+    for name, call in (("four_mechanisms_one_launch", joint), ("four_mechanisms_four_launches", separate),
+                       ("four_mechanisms_concurrent_launches", concurrent)):
+        _, ms = timed(call, inputs)
+        sub = sum(g.totals()["substeps"] for g in integs)
+        print(json.dumps({"batching": name, "mechanisms": list(presets), "cells_each": per, "dtype": "f64",
+                          "cells_per_s": len(presets) * per / (ms * 1e-3), "call_ms": ms,
+                          "block": int(integs[0].get_option("last_block")), "substeps": sub}), flush=True)
+
+
 def run_cfd_loop(args):
     """Learned scheduling + initial step at scale: the 100-species mechanism, 1,048,576
     cells (or --cells), 20 CFD steps of dt with the seeded mixing perturbation between
@@ -520,6 +601,9 @@ def main():
         return
     if args.refmap:
         run_refmap(args)
+        return
+    if args.batching:
+        run_batching(args)
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -174,7 +174,14 @@ typedef struct {
 /*
  * Integrates up to 8 jobs (each with its own mechanism handle) in ONE kernel
  * launch sharing one work queue. Options (precision, scheduler, block size)
- * are taken from jobs[0].h; per-cell statistics go to each job's handle.
+ * are taken from jobs[0].h; per-cell statistics go to each job's handle. The
+ * launch's CTA size and shared memory are those of the largest mechanism.
+ * With option "job_launch" = 1 on jobs[0].h, each job is instead integrated by
+ * its own launch with its own handle's options, on a stream the handle owns,
+ * forked from `stream` and joined back into it by events (the launches may run
+ * concurrently; `stream` orders after all of them). Errors: CHEM_ERR_INVALID_ARG
+ * (n_jobs outside 1..8, NULL or invalid jobs, a handle used twice, reference
+ * mapping on any handle in one-launch mode), as for chem_integrate otherwise.
  */
 chem_status chem_integrate_jobs(const chem_job* jobs, int32_t n_jobs, double dt, double rtol,
                                 double atol, void* stream);
@@ -213,10 +220,16 @@ chem_status chem_integrate_jobs(const chem_job* jobs, int32_t n_jobs, double dt,
  *                 analytical Jacobian replaces); also used by chem_eval_jacobian
  *   "pivoting"    FP64 form only: 1 = partial pivoting (default); 0 = Gaussian
  *                 elimination without row interchanges (a zero pivot rejects the step)
+ *   "job_launch"  chem_integrate_jobs only (read from jobs[0].h): 0 = one kernel
+ *                 launch for all jobs (default); 1 = one launch per job on
+ *                 concurrent streams, each with its own handle's options
  *   "time_kernel" 1 = record CUDA events on the stream around each integration
  *                 kernel launch (chem_get_kernel_ms); chem_integrate_noalloc
  *                 does not record them
  * Errors: CHEM_ERR_INVALID_ARG for an unknown key or out-of-range value.
+ * chem_get_option also reads "last_block" (read-only): the threads per CTA of
+ * the handle's last integration launch, as chosen by "block", the automatic
+ * choice or the autotuner (0 before the first launch).
  */
 chem_status chem_set_option(chem_handle h, const char* key, double value);
 chem_status chem_get_option(chem_handle h, const char* key, double* value);

@@ -499,6 +499,9 @@ extern "C" chem_status chem_destroy(chem_handle h) {
   if (h->kev0) cudaEventDestroy(h->kev0);
   if (h->kev1) cudaEventDestroy(h->kev1);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (void* p : h->allocations) cudaFree(p);
   if (h->d_tables) cudaFree(h->d_tables);
   delete h;
@@ -575,6 +578,7 @@ static const OptionDef kOptions[] = {
     {"time_kernel", &chem_handle_s::time_kernel, 0, 1},
     {"jacobian", &chem_handle_s::jac_fd, 0, 1},
     {"pivoting", &chem_handle_s::pivoting, 0, 1},
+    {"job_launch", &chem_handle_s::job_launch, 0, 1},
 };
 
 extern "C" chem_status chem_set_option(chem_handle h, const char* key, double value) {
@@ -599,6 +603,10 @@ extern "C" chem_status chem_set_option(chem_handle h, const char* key, double va
 
 extern "C" chem_status chem_get_option(chem_handle h, const char* key, double* value) {
   if (!h || !key || !value) return CHEM_ERR_INVALID_ARG;
+  if (std::strcmp(key, "last_block") == 0) {  // read-only: threads per CTA of the last launch
+    *value = (double)h->last_block;
+    return CHEM_OK;
+  }
   for (const auto& o : kOptions)
     if (std::strcmp(o.key, key) == 0) {
       *value = (double)(h->*(o.field));
@@ -710,6 +718,7 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
     s = chem_internal_autotune(h0, a, st, &block);
     if (s != CHEM_OK) return s;
   }
+  h0->last_block = block;
   int grid;
   if (a.sched == SCHED_PLAIN) {
     grid = (int)total;
@@ -838,6 +847,48 @@ extern "C" chem_status chem_integrate(chem_handle h, int64_t n_cells, double* T,
   return chem_internal_integrate(&j, 1, dt, rtol, atol, static_cast<cudaStream_t>(stream));
 }
 
+// Option job_launch = 1: one integration launch per job, each with its own handle's
+// options (block size and shared-memory layout fitted to its mechanism), on the
+// handles' own streams forked from and joined back into the caller's stream by
+// events, so that the kernels may run concurrently and a later job's CTAs fill the
+// SMs an earlier job's tail leaves idle.
+static chem_status integrate_jobs_concurrent(const chem_job* jobs, int32_t n_jobs, double dt, double rtol,
+                                             double atol, cudaStream_t st) {
+  chem_handle h0 = jobs[0].h;
+  for (int j = 0; j < n_jobs; ++j) {
+    chem_handle h = jobs[j].h;
+    if (!h->side) {
+      CHEM_CUDA(h0, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+      CHEM_CUDA(h0, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+      CHEM_CUDA(h0, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    }
+  }
+  CHEM_CUDA(h0, cudaEventRecord(h0->ev_fork, st));
+  chem_status s = CHEM_OK;
+  int launched = 0;
+  for (int j = 0; j < n_jobs && s == CHEM_OK; ++j) {
+    chem_handle h = jobs[j].h;
+    cudaError_t e = cudaStreamWaitEvent(h->side, h0->ev_fork, 0);
+    if (e != cudaSuccess) {
+      h0->err = cuda_msg("cudaStreamWaitEvent", e);
+      s = CHEM_ERR_CUDA;
+      break;
+    }
+    s = chem_internal_integrate(&jobs[j], 1, dt, rtol, atol, h->side);
+    if (s != CHEM_OK && h != h0) h0->err = h->err;
+    // joined even after an error, so that the caller's stream orders after all enqueued work
+    if (cudaEventRecord(h->ev_join, h->side) == cudaSuccess) ++launched;
+  }
+  for (int j = 0; j < launched; ++j) {
+    cudaError_t e = cudaStreamWaitEvent(st, jobs[j].h->ev_join, 0);
+    if (e != cudaSuccess && s == CHEM_OK) {
+      h0->err = cuda_msg("cudaStreamWaitEvent", e);
+      s = CHEM_ERR_CUDA;
+    }
+  }
+  return s;
+}
+
 extern "C" chem_status chem_integrate_jobs(const chem_job* jobs, int32_t n_jobs, double dt, double rtol,
                                            double atol, void* stream) {
   if (!jobs || n_jobs < 1 || n_jobs > kMaxJobs || !jobs[0].h) return CHEM_ERR_INVALID_ARG;
@@ -857,7 +908,9 @@ extern "C" chem_status chem_integrate_jobs(const chem_job* jobs, int32_t n_jobs,
         return CHEM_ERR_INVALID_ARG;
       }
   }
-  return chem_internal_integrate(jobs, n_jobs, dt, rtol, atol, static_cast<cudaStream_t>(stream));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (h0->job_launch == 1 && n_jobs > 1) return integrate_jobs_concurrent(jobs, n_jobs, dt, rtol, atol, st);
+  return chem_internal_integrate(jobs, n_jobs, dt, rtol, atol, st);
 }
 
 extern "C" chem_status chem_integrate_host(chem_handle h, int64_t n_cells, double* T, const double* p,

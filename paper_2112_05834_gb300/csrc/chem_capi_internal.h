@@ -30,6 +30,7 @@ struct chem_handle_s {
   int h0mode = 0;
   int max_steps = 100000;
   int block = 0;  // 0: chosen per call by chem_internal_pick_block
+  int last_block = 0;  // threads per CTA of the last integration launch (option "last_block", read-only)
   int ctas_per_sm = 0;
   int graph = 0;
   int autotune = 0;
@@ -40,6 +41,9 @@ struct chem_handle_s {
   int time_kernel = 0;                    // option "time_kernel": events around the integration launch
   int jac_fd = 0;                         // option "jacobian": 1 = forward differences (FP64 form)
   int pivoting = 1;                       // option "pivoting": 0 = no row interchanges (FP64 form)
+  int job_launch = 0;                     // option "job_launch": 1 = one launch per job, concurrent streams
+  cudaStream_t side = nullptr;            // the handle's stream for concurrent jobs
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t kev0 = nullptr, kev1 = nullptr;
   bool kev_recorded = false;
   // per-cell statistics of the last call

@@ -373,6 +373,32 @@ def test_multi_mechanism_single_launch(pkg, orc):
         _assert_bound(s["T"][sub], s["Y"][sub], ref, m.species[0])
 
 
+def test_multi_mechanism_concurrent_launches(pkg):
+    """Option job_launch = 1: one launch per job on streams forked from the caller's,
+    each with its own handle's block size; per-cell results and statistics bitwise equal
+    to separate calls, and work the caller enqueues afterwards on its stream sees them."""
+    names = [("h2_10", synth.ATM), ("c_32", 60e5), ("c_54", 60e5), ("c_100", 40e5)]
+    dt = 1e-6
+    jobs, singles = [], []
+    for i, (nm, p) in enumerate(names):
+        m = synth.mechanism_preset(nm)
+        st = synth.gen_states(m, 300 + 7 * i, seed=20 + i, p=p, classes=synth.MIXED_CLASSES)
+        integ = pkg.Integrator(m, precision=1, job_launch=1 if i == 0 else 0)
+        jobs.append((integ, _dev(st.T), _dev(st.p), _dev(st.Y)))
+        singles.append(_run(pkg, m, st, dt, precision=1))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        pkg.integrate_jobs(jobs, dt, RTOL, ATOL, stream=s)
+        sums = [Y.sum(dim=1) for (_, _, _, Y) in jobs]  # ordered after the jobs on s
+    s.synchronize()
+    for (integ, T, p, Y), r, sm in zip(jobs, singles, sums):
+        np.testing.assert_array_equal(T.cpu().numpy(), r["T"])
+        np.testing.assert_array_equal(Y.cpu().numpy(), r["Y"])
+        np.testing.assert_array_equal(sm.cpu().numpy(), Y.sum(dim=1).cpu().numpy())
+        st = integ.stats(T.shape[0])
+        np.testing.assert_array_equal(st["substeps"].cpu().numpy(), r["substeps"])
+
+
 # ------------------------------------------------------------------ edge cases
 def test_edge_cases(pkg):
     m = synth.mechanism_preset("h2_10")
