@@ -865,7 +865,7 @@ static chem_status integrate_jobs_concurrent(const chem_job* jobs, int32_t n_job
   }
   CHEM_CUDA(h0, cudaEventRecord(h0->ev_fork, st));
   chem_status s = CHEM_OK;
-  int launched = 0;
+  bool joined[kMaxJobs] = {};
   for (int j = 0; j < n_jobs && s == CHEM_OK; ++j) {
     chem_handle h = jobs[j].h;
     cudaError_t e = cudaStreamWaitEvent(h->side, h0->ev_fork, 0);
@@ -877,9 +877,10 @@ static chem_status integrate_jobs_concurrent(const chem_job* jobs, int32_t n_job
     s = chem_internal_integrate(&jobs[j], 1, dt, rtol, atol, h->side);
     if (s != CHEM_OK && h != h0) h0->err = h->err;
     // joined even after an error, so that the caller's stream orders after all enqueued work
-    if (cudaEventRecord(h->ev_join, h->side) == cudaSuccess) ++launched;
+    joined[j] = cudaEventRecord(h->ev_join, h->side) == cudaSuccess;
   }
-  for (int j = 0; j < launched; ++j) {
+  for (int j = 0; j < n_jobs; ++j) {
+    if (!joined[j]) continue;
     cudaError_t e = cudaStreamWaitEvent(st, jobs[j].h->ev_join, 0);
     if (e != cudaSuccess && s == CHEM_OK) {
       h0->err = cuda_msg("cudaStreamWaitEvent", e);
