@@ -225,24 +225,67 @@ def phase_rooflines(m, hd, n, mlp_ms):
     return out
 
 
+def cpu_model():
+    """The host CPU's model name (x86: "model name"; Arm: implementer / part codes)."""
+    import platform
+
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields.setdefault(k.strip().lower(), v.strip())
+    except OSError:
+        pass
+    if "model name" in fields:
+        return fields["model name"]
+    if "cpu part" in fields:
+        return f"{platform.machine()} (CPU implementer {fields.get('cpu implementer', '?')}, part {fields['cpu part']})"
+    return platform.processor() or platform.machine()
+
+
+_HOST_THREADS = []
+
+
+def host_threads():
+    """The oracle's OpenMP thread count, read once: the oracle's integrate sets the
+    process-wide count when given n_threads, so a later read would see the last value."""
+    if not _HOST_THREADS:
+        import oracle
+
+        _HOST_THREADS.append(oracle.max_threads())
+    return _HOST_THREADS[0]
+
+
+def _oracle_rate(m, st, dt, seconds, order, threads, chunk):
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds and done < order.size:
+        idx = order[done:done + chunk]
+        import oracle
+
+        oracle.integrate(m, st.T[idx], st.p[idx], st.Y[idx], dt, RTOL, ATOL, n_threads=threads)
+        done += idx.size
+    return done, time.perf_counter() - t0
+
+
 def cpu_baseline(m, st, dt, seconds, seed=0):
-    """Oracle on a bounded uniform sample of the workload's cells (all host cores)."""
+    """Oracle on a bounded uniform sample of the workload's cells (all host cores), plus a
+    single-thread rate on a fifth of the time budget (another sample of the same cells)."""
     import oracle
 
     oracle.build()
     rng = np.random.default_rng(seed)
     order = rng.permutation(st.T.shape[0])
-    done, t0 = 0, time.perf_counter()
-    chunk = 64
-    threads = oracle.max_threads()
-    while time.perf_counter() - t0 < seconds and done < order.size:
-        idx = order[done:done + chunk]
-        oracle.integrate(m, st.T[idx], st.p[idx], st.Y[idx], dt, RTOL, ATOL, n_threads=threads)
-        done += idx.size
-    el = time.perf_counter() - t0
+    threads = host_threads()
+    done, el = _oracle_rate(m, st, dt, seconds, order, threads, 64)
+    rest = order[done:] if done < order.size else order
+    done1, el1 = _oracle_rate(m, st, dt, seconds / 5.0, rest, 1, 4)
     return {"value": done / el, "unit": "cells*step/s", "cores": threads, "kind": "oracle",
             "sample": f"{done} uniformly sampled cells of the {st.T.shape[0]}-cell batch, "
-                      f"{el:.1f} s on {threads} threads"}
+                      f"{el:.1f} s on {threads} threads",
+            "single_thread": {"value": done1 / el1, "sample": f"{done1} further cells, {el1:.1f} s on 1 thread"},
+            "cpu_model": cpu_model()}
 
 
 # ---------------------------------------------------------------------------- GPU arm
@@ -627,7 +670,8 @@ def main():
                     "config": {"workload": args.workload, "n_cells": int(st.T.shape[0]),
                                "mechanism": f"{m.n_species} species / {m.n_reactions} reactions"},
                     "cpu_baseline": {"value": v, "unit": "cells*step/s", "cores": cb["cores"], "kind": "oracle",
-                                     "sample": cb["sample"]},
+                                     "sample": cb["sample"], "single_thread": cb["single_thread"],
+                                     "cpu_model": cb["cpu_model"]},
                     "e2e": {"value": v, "unit": "cells*step/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
             print(json.dumps(line))
         return
