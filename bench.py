@@ -231,13 +231,13 @@ def cpu_model():
 
     fields = {}
     try:
-        with open("/proc/cpuinfo") as f:
+        with open("/proc/cpuinfo", errors="replace") as f:
             for line in f:
                 if ":" in line:
                     k, v = line.split(":", 1)
                     fields.setdefault(k.strip().lower(), v.strip())
-    except OSError:
-        pass
+    except Exception:  # the model name is informative only
+        fields = {}
     if "model name" in fields:
         return fields["model name"]
     if "cpu part" in fields:
