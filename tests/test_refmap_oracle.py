@@ -11,7 +11,8 @@ and the selection rule fix, independent of the oracle's own formulas.
 - The selection rule by hand on small cases (zone boundary inclusive, NaN excluded,
   lowest-index reference, temperature window, empty zone).
 - A zone cell identical to the reference ends where the reference (and its own plain
-  integration) ends; mapped cells keep their Z and sum of Y.
+  integration) ends; mapped cells keep their Z and sum of Y; a failed reference maps
+  nothing (mapped cells keep their initial state and take its status).
 """
 import numpy as np
 import pytest
@@ -34,7 +35,6 @@ def test_beta_zero_at_stoichiometry(preset):
     nu_o2 = f["C"] + f["H"] / 4.0 - f["O"] / 2.0
     assert nu_o2 > 0
     K = m.n_species
-    scale = []
     for x_n2 in (0.0, 3.76 * nu_o2):
         X = np.zeros(K)
         X[m.roles["fuel"]] = 1.0
@@ -125,3 +125,16 @@ def test_mapped_cells_keep_Z_and_sum(oracle_lib):
     plain = oracle_lib.integrate(m, st.T[solve], st.p[solve], st.Y[solve], dt)
     assert np.array_equal(res["T"][solve], plain["T"])
     assert np.array_equal(res["Y"][solve], plain["Y"])
+
+
+def test_failed_reference_leaves_mapped_cells(oracle_lib):
+    """A reference that fails (step budget of one step) maps nothing: the mapped cells keep
+    their initial state and take the reference's status."""
+    m, st, dt = synth.workload("c54_65k_oxzone", n_cells=40, state_seed=5)
+    yf, yo = synth.streams(m)
+    res = rm.integrate_mapped(m, st.T, st.p, st.Y, dt, yf, yo, 0.0, 1e-4, 10.0, max_steps=1)
+    mp, r = res["mapped"], res["ref"]
+    assert r >= 0 and mp.sum() >= 3
+    assert res["status"][r] != 0
+    assert np.all(res["status"][mp] == res["status"][r])
+    assert np.array_equal(res["Y"][mp], st.Y[mp]) and np.array_equal(res["T"][mp], st.T[mp])
