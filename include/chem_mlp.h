@@ -74,6 +74,17 @@ chem_status chem_mlp_gradient(chem_mlp m, int64_t n, const double* T, const doub
                               const int32_t* substeps, const double* h_first, float* loss_host,
                               float* grad_host, void* stream);
 
+/*
+ * One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias corrections by the model's
+ * own count of updates, which chem_mlp_train advances too) on the FP32 master
+ * weights with a caller-supplied gradient, then the BF16 copy the kernels read is
+ * refreshed. grad_host: host floats in the order and length of chem_mlp_gradient's
+ * output (W1, b1, W2, b2, W3, b3), e.g. a gradient accumulated over several batches.
+ * Normalisation is untouched. Synchronises `stream`. Errors: CHEM_ERR_INVALID_ARG
+ * (NULL, lr not finite and > 0), CHEM_ERR_CUDA.
+ */
+chem_status chem_mlp_apply_gradient(chem_mlp m, const float* grad_host, double lr, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,6 +13,9 @@ method's own logs):
   targets   t = [ln substeps, ln h_first], standardised ts = (t - mu_t) / sd_t
   loss      L = 1/(2B) sum_b sum_o (out_bo - ts_bo)^2
 GELU(z) = z Phi(z) with the standard normal CDF Phi (the exact form).
+
+Optimizer: Adam (D. P. Kingma and J. Ba, "Adam: a method for stochastic
+optimization", ICLR 2015, Algorithm 1), one step per call of ``adam_step``.
 """
 from __future__ import annotations
 
@@ -99,3 +102,20 @@ def unflatten(vec, D, H=128):
         out[k] = np.asarray(vec[o:o + n], dtype=np.float64).reshape(shapes[k])
         o += n
     return out
+
+
+def adam_step(w, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update in FP64 (Kingma & Ba 2015, Algorithm 1).
+
+    ``t`` is the number of updates taken before this one; the moments m, v start at
+    zero. Biased first and second moment estimates, their bias corrections by
+    1 - beta^t, and the parameter step lr * m_hat / (sqrt(v_hat) + eps).
+    Returns (w_new, m_new, v_new, t + 1); the inputs are not modified."""
+    w = np.asarray(w, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    t1 = t + 1
+    m1 = beta1 * np.asarray(m, dtype=np.float64) + (1.0 - beta1) * g
+    v1 = beta2 * np.asarray(v, dtype=np.float64) + (1.0 - beta2) * g * g
+    m_hat = m1 / (1.0 - beta1 ** t1)
+    v_hat = v1 / (1.0 - beta2 ** t1)
+    return w - lr * m_hat / (np.sqrt(v_hat) + eps), m1, v1, t1

@@ -55,6 +55,7 @@ SIGNATURES = {
     "chem_mlp_get_params": (C.c_int, [_P, _P, _P]),
     "chem_mlp_set_params": (C.c_int, [_P, _P, _I64]),
     "chem_mlp_gradient": (C.c_int, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "chem_mlp_apply_gradient": (C.c_int, [_P, _P, _D, _P]),
 }
 
 _lib = None
@@ -395,6 +396,16 @@ class CostModel:
         _check(load().chem_mlp_gradient(self.h, n, _dptr(T), _dptr(p), _dptr(Y), _dptr(substeps), _dptr(h_first),
                                         C.byref(loss), g.ctypes.data_as(C.c_void_p), _stream_ptr(stream)))
         return loss.value, g
+
+    def apply_gradient(self, grad, lr=1e-3, stream=None):
+        """One Adam update of the master weights with a given gradient (host floats in
+        the order of ``gradient``'s output)."""
+        g = np.ascontiguousarray(grad, dtype=np.float32)
+        D = self.K + 2
+        if g.size != 128 * D + 128 + 128 * 128 + 128 + 2 * 128 + 2:
+            raise ValueError("gradient has the wrong length")
+        _check(load().chem_mlp_apply_gradient(self.h, g.ctypes.data_as(C.c_void_p), float(lr),
+                                              _stream_ptr(stream)))
 
     def attach(self, integrator):
         _check(load().chem_mlp_attach(integrator.h, self.h), integrator.h)

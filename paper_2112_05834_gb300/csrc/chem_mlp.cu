@@ -604,6 +604,13 @@ static chem_status fwd_bwd(chem_mlp m, int rows, cudaStream_t st, float* loss_de
   return mlp_cuda(m, cudaGetLastError(), "mlp backward");
 }
 
+// Adam's bias corrections 1 - beta^t for the FP32 betas the kernel uses, evaluated in
+// double and rounded once (1 - beta2^t in float loses ~1e-5 relative for small t).
+static void adam_corrections(float b1, float b2, int64_t t, float* c1, float* c2) {
+  *c1 = (float)(1.0 - std::pow((double)b1, (double)t));
+  *c2 = (float)(1.0 - std::pow((double)b2, (double)t));
+}
+
 static chem_status set_normalisation(chem_mlp m, int64_t n, const double* T, const double* p, const double* Y,
                                      const int32_t* sub, const double* hf, cudaStream_t st) {
   const int D = m->D;
@@ -677,7 +684,8 @@ extern "C" chem_status chem_mlp_train(chem_mlp m, int64_t n, const double* T, co
       s = fwd_bwd(m, rows, st, loss_d + bi);
       if (s != CHEM_OK) return s;
       ++m->adam_t;
-      const float c1 = 1.0f - std::pow(b1, (float)m->adam_t), c2 = 1.0f - std::pow(b2, (float)m->adam_t);
+      float c1, c2;
+      adam_corrections(b1, b2, m->adam_t, &c1, &c2);
       k_adam<<<64, 256, 0, st>>>(m->w, m->g, m->m, m->v, m->wb, m->nw, (float)lr, b1, b2, eps, c1, c2);
     }
     // the host permutation buffer is reused next epoch: wait, and collect the batch losses
@@ -719,6 +727,20 @@ extern "C" chem_status chem_mlp_gradient(chem_mlp m, int64_t n, const double* T,
   MLP_TRY(m, cudaStreamSynchronize(st));
   cudaFree(loss_d);
   if (loss_host) *loss_host = l;
+  return CHEM_OK;
+}
+
+extern "C" chem_status chem_mlp_apply_gradient(chem_mlp m, const float* grad_host, double lr, void* stream) {
+  if (!m || !grad_host || !(lr > 0.0) || !std::isfinite(lr)) return CHEM_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  MLP_TRY(m, cudaMemcpyAsync(m->g, grad_host, m->nw * 4, cudaMemcpyHostToDevice, st));
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  ++m->adam_t;
+  float c1, c2;
+  adam_corrections(b1, b2, m->adam_t, &c1, &c2);
+  k_adam<<<64, 256, 0, st>>>(m->w, m->g, m->m, m->v, m->wb, m->nw, (float)lr, b1, b2, eps, c1, c2);
+  MLP_TRY(m, cudaGetLastError());
+  MLP_TRY(m, cudaStreamSynchronize(st));
   return CHEM_OK;
 }
 
