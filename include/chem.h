@@ -133,30 +133,38 @@ chem_status chem_integrate_host(chem_handle h, int64_t n_cells, double* T, const
  * counterpart: this exists for users of this library, not for the method.
  *
  * chem_integrate may grow handle-owned device buffers with cudaMalloc/cudaFree.
- * Callers that cannot allow that -- code enqueueing work while a stream is being
- * captured into a CUDA graph (allocation is not permitted during capture),
- * applications whose device memory is fixed up front by their own pool, and
- * callers that cannot accept the device synchronisation an allocation or free
- * may imply -- use this entry point instead. It allocates nothing: the
- * integration kernel's scratch (work-queue counter and per-cell statistics) lives
- * in one fixed-size device array inside the library, sized for
- * CHEM_NOALLOC_MAX_CELLS cells (about 1.3 MB), which every GPU that loads the
- * library holds until the process exits.
+ * Callers that cannot allow that -- applications whose device memory is fixed up
+ * front by their own pool or budget (a CFD code that reserves the GPU's memory
+ * for its fields and solvers at start-up, where a late cudaMalloc fails or
+ * evicts its pool), and callers inside a time-step loop that cannot accept the
+ * device synchronisation an allocation or free may imply while other streams are
+ * busy -- use this entry point instead. It allocates nothing: the integration
+ * kernel's scratch (work-queue counter and per-cell statistics) lives in one
+ * fixed-size device array inside the library, sized for CHEM_NOALLOC_MAX_CELLS
+ * cells (about 1.3 MB), which every GPU that loads the library holds until the
+ * process exits.
  *
  * Arguments, layout and results are those of chem_integrate (device pointers,
- * in-place T and Y, stream-ordered). The handle's precision, scheduler, block,
- * ir_sweeps, max_steps and ctas_per_sm options apply; cells are taken in index
- * order with the starting-step heuristic (the learned order and initial step,
- * the autotuner and graph capture need handle-owned buffers and are not used).
- * Per-cell statistics are not reported by this path.
+ * in-place T and Y, stream-ordered), and for the same handle options and block
+ * size the results are bitwise those of chem_integrate. The handle's precision,
+ * scheduler, block, ir_sweeps, max_steps and ctas_per_sm options apply; cells
+ * are taken in index order with the starting-step heuristic (the learned order
+ * and initial step, the autotuner and CUDA-graph replay need handle-owned
+ * buffers and are not used).
+ *
+ * After this call, chem_get_stats and chem_get_totals on the handle report this
+ * call's cells (substeps, rejections, first step, status -- a failed cell keeps
+ * its last accepted state, as in chem_integrate) by reading the fixed array: read
+ * them before another call of this entry point on the same device overwrites it.
  *
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
  * capture. All calls share the one array and it keeps the last call's contents:
  * the call clears what must start at zero (the queue counter) on `stream`, and
  * calls that overlap on the GPU (concurrent streams or handles) race on it.
- * Errors: CHEM_ERR_INVALID_ARG as for chem_integrate, and for
- * n_cells > CHEM_NOALLOC_MAX_CELLS (split the batch); CHEM_ERR_CUDA.
+ * Errors: CHEM_ERR_INVALID_ARG as for chem_integrate, for
+ * n_cells > CHEM_NOALLOC_MAX_CELLS (split the batch) and for a handle with
+ * reference mapping on; CHEM_ERR_CUDA.
  */
 #define CHEM_NOALLOC_MAX_CELLS 65536
 chem_status chem_integrate_noalloc(chem_handle h, int64_t n_cells, double* T, const double* p, double* Y,

@@ -625,10 +625,7 @@ extern "C" int32_t chem_n_reactions(chem_handle h) { return h ? h->I_user : -1; 
 // ---------------------------------------------------------------------------
 // integration
 // ---------------------------------------------------------------------------
-static bool bad_tol(double dt, double rtol, double atol) {
-  return !(dt > 0.0) || !std::isfinite(dt) || !(rtol > 0.0) || !std::isfinite(rtol) || !(atol >= 0.0) ||
-         !std::isfinite(atol);
-}
+static bool bad_tol(double dt, double rtol, double atol) { return chem_internal_bad_tol(dt, rtol, atol); }
 
 chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double dt, double rtol,
                                     double atol, cudaStream_t st) {
@@ -637,6 +634,7 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
   for (int j = 0; j < n_jobs; ++j) {
     rm = rm || jobs[j].h->refmap;
     jobs[j].h->rm_last_n = -1;
+    jobs[j].h->noalloc_n = -1;
   }
   if (rm && (n_jobs != 1 || h0->scheduler != SCHED_QUEUE)) {
     h0->err = "chem_integrate: reference mapping needs one job and the queue scheduler";
@@ -950,18 +948,31 @@ extern "C" chem_status chem_integrate_host(chem_handle h, int64_t n_cells, doubl
 // ---------------------------------------------------------------------------
 // statistics
 // ---------------------------------------------------------------------------
+chem_status chem_internal_stats_view(chem_handle h, chem_stats_view* v) {
+  if (h->noalloc_n >= 0) return chem_internal_noalloc_stats(h, h->noalloc_n, v);
+  v->n = h->last_n;
+  v->substeps = h->d_sub;
+  v->rejects = h->d_rej;
+  v->status = h->d_status;
+  v->h_first = h->d_hfirst;
+  return CHEM_OK;
+}
+
 extern "C" chem_status chem_get_stats(chem_handle h, void* stream, int32_t* substeps, int32_t* rejects,
                                       double* h_first, int32_t* cell_status) {
   if (!h) return CHEM_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int64_t n = h->last_n;
+  chem_stats_view v;
+  chem_status vs = chem_internal_stats_view(h, &v);
+  if (vs != CHEM_OK) return vs;
+  const int64_t n = v.n;
   if (n == 0) return CHEM_OK;
-  if (substeps) CHEM_CUDA(h, cudaMemcpyAsync(substeps, h->d_sub, n * 4, cudaMemcpyDeviceToDevice, st));
-  if (rejects) CHEM_CUDA(h, cudaMemcpyAsync(rejects, h->d_rej, n * 4, cudaMemcpyDeviceToDevice, st));
-  if (h_first) CHEM_CUDA(h, cudaMemcpyAsync(h_first, h->d_hfirst, n * 8, cudaMemcpyDeviceToDevice, st));
-  if (cell_status) CHEM_CUDA(h, cudaMemcpyAsync(cell_status, h->d_status, n * 4, cudaMemcpyDeviceToDevice, st));
+  if (substeps) CHEM_CUDA(h, cudaMemcpyAsync(substeps, v.substeps, n * 4, cudaMemcpyDeviceToDevice, st));
+  if (rejects) CHEM_CUDA(h, cudaMemcpyAsync(rejects, v.rejects, n * 4, cudaMemcpyDeviceToDevice, st));
+  if (h_first) CHEM_CUDA(h, cudaMemcpyAsync(h_first, v.h_first, n * 8, cudaMemcpyDeviceToDevice, st));
+  if (cell_status) CHEM_CUDA(h, cudaMemcpyAsync(cell_status, v.status, n * 4, cudaMemcpyDeviceToDevice, st));
   std::vector<int32_t> hs(n);
-  CHEM_CUDA(h, cudaMemcpyAsync(hs.data(), h->d_status, n * 4, cudaMemcpyDeviceToHost, st));
+  CHEM_CUDA(h, cudaMemcpyAsync(hs.data(), v.status, n * 4, cudaMemcpyDeviceToHost, st));
   CHEM_CUDA(h, cudaStreamSynchronize(st));
   for (int64_t i = 0; i < n; ++i)
     if (hs[i] != CHEM_CELL_OK) {
@@ -975,12 +986,15 @@ extern "C" chem_status chem_get_totals(chem_handle h, void* stream, int64_t* n_c
                                        int64_t* rejects, int64_t* failed) {
   if (!h) return CHEM_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int64_t n = h->last_n;
+  chem_stats_view v;
+  chem_status vs = chem_internal_stats_view(h, &v);
+  if (vs != CHEM_OK) return vs;
+  const int64_t n = v.n;
   std::vector<int32_t> a(n), b(n), c(n);
   if (n > 0) {
-    CHEM_CUDA(h, cudaMemcpyAsync(a.data(), h->d_sub, n * 4, cudaMemcpyDeviceToHost, st));
-    CHEM_CUDA(h, cudaMemcpyAsync(b.data(), h->d_rej, n * 4, cudaMemcpyDeviceToHost, st));
-    CHEM_CUDA(h, cudaMemcpyAsync(c.data(), h->d_status, n * 4, cudaMemcpyDeviceToHost, st));
+    CHEM_CUDA(h, cudaMemcpyAsync(a.data(), v.substeps, n * 4, cudaMemcpyDeviceToHost, st));
+    CHEM_CUDA(h, cudaMemcpyAsync(b.data(), v.rejects, n * 4, cudaMemcpyDeviceToHost, st));
+    CHEM_CUDA(h, cudaMemcpyAsync(c.data(), v.status, n * 4, cudaMemcpyDeviceToHost, st));
   }
   CHEM_CUDA(h, cudaStreamSynchronize(st));
   int64_t s1 = 0, s2 = 0, s3 = 0;

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -49,6 +50,7 @@ struct chem_handle_s {
   // per-cell statistics of the last call
   int64_t stats_cap = 0;
   int64_t last_n = 0;
+  int64_t noalloc_n = -1;  // cells of the last call when it was chem_integrate_noalloc, else -1
   int32_t* d_sub = nullptr;
   int32_t* d_rej = nullptr;
   int32_t* d_status = nullptr;
@@ -94,6 +96,23 @@ struct chem_handle_s {
   int autotuned_block = 128;
   std::string err;
 };
+
+// dt, rtol, atol outside the accepted range (dt > 0, rtol > 0, atol >= 0, all finite)
+inline bool chem_internal_bad_tol(double dt, double rtol, double atol) {
+  return !(dt > 0.0) || !std::isfinite(dt) || !(rtol > 0.0) || !std::isfinite(rtol) || !(atol >= 0.0) ||
+         !std::isfinite(atol);
+}
+
+// Device arrays holding the per-cell statistics of a handle's last call: its own
+// buffers, or the allocation-free entry point's fixed array after a call of that
+// entry point (the array's current contents: the last such call on the device).
+struct chem_stats_view {
+  int64_t n;
+  const int32_t *substeps, *rejects, *status;
+  const double* h_first;
+};
+chem_status chem_internal_stats_view(chem_handle h, chem_stats_view* v);
+chem_status chem_internal_noalloc_stats(chem_handle h, int64_t n, chem_stats_view* v);
 
 chem_status chem_internal_alloc(chem_handle h, void* pp, size_t bytes);
 chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double dt, double rtol, double atol,

@@ -3,11 +3,12 @@
 //
 // chem_integrate grows handle-owned buffers on demand (per-cell statistics, the
 // work-queue counter, learned-order scratch), which may call cudaMalloc and
-// cudaFree. Some callers cannot allow that: code that enqueues work while a
-// stream is being captured into a CUDA graph (allocation calls are not
-// permitted during capture), applications whose device memory is fixed up front
-// by their own pool or budget, and callers that cannot accept the device-wide
-// synchronisation a cudaMalloc/cudaFree may imply in the middle of a time step.
+// cudaFree. Some callers cannot allow that: applications whose device memory is
+// fixed up front by their own pool or budget (a CFD code that reserves the GPU's
+// memory for its fields and solvers at start-up, where a late cudaMalloc fails
+// or evicts its pool), and callers inside a time-step loop that cannot accept
+// the device-wide synchronisation a cudaMalloc/cudaFree may imply while other
+// streams are busy.
 //
 // This variant keeps the scratch of the integration kernel (the work-queue
 // counter and the per-cell statistics it writes) in one file-scope device array
@@ -74,7 +75,7 @@ chem_status scratch_address(chem_handle h, unsigned char** out) {
 extern "C" chem_status chem_integrate_noalloc(chem_handle h, int64_t n_cells, double* T, const double* p,
                                               double* Y, double dt, double rtol, double atol, void* stream) {
   if (!h) return CHEM_ERR_INVALID_ARG;
-  if (n_cells < 0 || (n_cells > 0 && (!T || !p || !Y)) || !(dt > 0.0) || !(rtol > 0.0) || !(atol >= 0.0)) {
+  if (n_cells < 0 || (n_cells > 0 && (!T || !p || !Y)) || chem_internal_bad_tol(dt, rtol, atol)) {
     h->err = "chem_integrate_noalloc: invalid argument (n_cells < 0, NULL array, or dt/rtol/atol out of range)";
     return CHEM_ERR_INVALID_ARG;
   }
@@ -87,6 +88,12 @@ extern "C" chem_status chem_integrate_noalloc(chem_handle h, int64_t n_cells, do
     h->err = "chem_integrate_noalloc: reference mapping needs handle-owned buffers; use chem_integrate";
     return CHEM_ERR_INVALID_ARG;
   }
+  // from here on the handle's statistics queries read this call's cells from the
+  // fixed array; the last-call cost order and carried-over steps of the handle's
+  // own buffers no longer describe the cells it was last given
+  h->noalloc_n = n_cells;
+  h->cost_valid = false;
+  h->hlast_valid = false;
   if (n_cells == 0) return CHEM_OK;
   unsigned char* base = nullptr;
   chem_status s = scratch_address(h, &base);
@@ -143,5 +150,21 @@ extern "C" chem_status chem_integrate_noalloc(chem_handle h, int64_t n_cells, do
     h->err = std::string("chem_integrate_noalloc: ") + cudaGetErrorString(e);
     return CHEM_ERR_CUDA;
   }
+  return CHEM_OK;
+}
+
+chem_status chem_internal_noalloc_stats(chem_handle h, int64_t n, chem_stats_view* v) {
+  if (n == 0) {
+    *v = chem_stats_view{0, nullptr, nullptr, nullptr, nullptr};
+    return CHEM_OK;
+  }
+  unsigned char* base = nullptr;
+  chem_status s = scratch_address(h, &base);
+  if (s != CHEM_OK) return s;
+  v->n = n;
+  v->substeps = reinterpret_cast<const int32_t*>(base + kCounterBytes);
+  v->rejects = reinterpret_cast<const int32_t*>(base + kCounterBytes + kI32Bytes);
+  v->status = reinterpret_cast<const int32_t*>(base + kCounterBytes + 2 * kI32Bytes);
+  v->h_first = reinterpret_cast<const double*>(base + kCounterBytes + 3 * kI32Bytes);
   return CHEM_OK;
 }
