@@ -117,6 +117,10 @@ __device__ const double2 g_exp2_tab[32] = {
 __device__ __noinline__ double exp_outside(double x) { return exp(x); }
 
 constexpr double kInvLn10 = 0.43429448190325176;  // 1 / ln 10
+// Largest |G/RT| of a species for which the reverse-rate ratio is formed as a
+// product of per-species factors exp(+-G/RT): four factors stay within e^+-600.
+constexpr double kBigGRT = 150.0;
+constexpr double kLnRcP0 = 4.407418589020958;  // ln(Rc / P0), cgs
 
 __device__ __forceinline__ double xexp(double x, const double2* tab) {
   if ((__double2hiint(x) & 0x7fffffff) >= 0x40850000) return exp_outside(x);  // |x| >= 672, inf, NaN
@@ -557,6 +561,7 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
     if (c.lane == 0) {
       c.red[SC_LOGT] = lg;
       c.red[SC_INVT] = invT0;
+      c.red[SC_FLAG] = 0.0;  // set below when some |G/RT| is too large for the factor products
     }
   }
   {
@@ -586,9 +591,12 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
     double sr = a[11] * logT + T * (a[12] + T * (a[13] + T * (a[14] + T * a[15]))) + a[16];
     c.cpR[k] = cp;
     c.hRT[k] = h;
-    const double e = xexp(h - sr, c.etab);
+    const double g = h - sr;
+    const double e = xexp(g, c.etab);
     c.eg[k] = e;
     c.ieg[k] = xrcp(e);
+    c.ek[k] = g;  // G/RT (the slot is the Jacobian assembly's, unused until then)
+    if (fabs(g) > kBigGRT) c.red[SC_FLAG] = 1.0;
     const double Ck = s.rho * y[1 + k] * m.invW[k];
     c.C[k] = Ck;
     // float-float copy of C for the third-body sums (the slot of d_k, which the
@@ -599,6 +607,10 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
   __syncthreads();
   const double cRT = kRc * T / kP0;  // (P0 / (Rc T))^-1
   const double icRT = kP0 * invT / kRc;
+  // A cell with some |G/RT| > kBigGRT (very low T with large formation enthalpies)
+  // takes one exponential of the summed exponent per reaction instead of the product
+  // of four species factors, whose partial products could overflow or underflow.
+  const bool bigG = c.red[SC_FLAG] != 0.0;
   // 32-reaction chunks of one kind each, dealt to the warps by estimated work
   const int* cs = m.chunk_sched[NW == 2 ? 0 : NW == 4 ? 1 : 2];
   for (int pos = cs[c.warp]; pos < cs[c.warp + 1]; ++pos) {
@@ -626,10 +638,19 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
     double ratio = 0.0;
     const int rv = m.rev[i];
     if (rv & 1) {
-      ratio = c.eg[sl.z] * c.ieg[sl.x];
-      if (sl.w >= 0) ratio *= c.eg[sl.w];
-      if (sl.y >= 0) ratio *= c.ieg[sl.y];
-      ratio *= (rv >> 1) == 2 ? cRT : (rv >> 1) == 0 ? icRT : 1.0;
+      if (!bigG) {
+        ratio = c.eg[sl.z] * c.ieg[sl.x];
+        if (sl.w >= 0) ratio *= c.eg[sl.w];
+        if (sl.y >= 0) ratio *= c.ieg[sl.y];
+        ratio *= (rv >> 1) == 2 ? cRT : (rv >> 1) == 0 ? icRT : 1.0;
+      } else {
+        double dg = c.ek[sl.z] - c.ek[sl.x];
+        if (sl.w >= 0) dg += c.ek[sl.w];
+        if (sl.y >= 0) dg -= c.ek[sl.y];
+        const double lc = logT + kLnRcP0;  // ln(Rc T / P0)
+        dg += (rv >> 1) == 2 ? lc : (rv >> 1) == 0 ? -lc : 0.0;
+        ratio = xexp(dg, c.etab);
+      }
     }
     double Mc = 0.0, phi = 1.0;
     double dk_dM = 0.0, dlnk = (ar.y + ar.z * invT) * invT, dk_dT = 0.0;

@@ -103,6 +103,51 @@ def test_jacobian_parity(pkg, orc, name):
             assert err.max() <= tol, (name, precision, c, err.max())
 
 
+def _large_gibbs_mechanism():
+    """The 54-species mechanism with every formation enthalpy (NASA a6) scaled so the
+    largest |a6| is 1.8e5 K: at 300 K the species' |G/RT| reach about 600. Scaling all
+    a6 by one factor keeps each reaction's enthalpy sign, so reverse rates stay finite."""
+    import copy
+
+    m = copy.deepcopy(synth.mechanism_preset("c_54"))
+    s = 1.8e5 / np.abs(m.nasa_lo[:, 5]).max()
+    m.nasa_lo[:, 5] *= s
+    m.nasa_hi[:, 5] *= s
+    return m
+
+
+def test_rhs_jacobian_large_gibbs_parity(pkg, orc):
+    """Cells between 300 K and 2500 K of a mechanism whose species reach |G/RT| ~ 600
+    at 300 K: the kernels' reverse-rate ratio (normally a product of per-species
+    factors exp(+-G/RT), whose partial products would leave the double range here)
+    must match the oracle's one exponential of the reaction's Gibbs energy change, for
+    the RHS (1e-11) and the Jacobian (1e-10), FP64 and mixed forms."""
+    m = _large_gibbs_mechanism()
+    st = _states(m, n=16)
+    st.T[:] = np.geomspace(300.0, 2500.0, 16)
+    M = orc.Mech(m)
+    g_rt = np.array([[orc.thermo(M, T)[1][k] - orc.thermo(M, T)[2][k] for k in range(m.n_species)]
+                     for T in st.T[:2]])
+    assert np.abs(g_rt).max() > 300.0  # the range the factor products cannot hold
+    nu = np.abs(m.net_stoich())
+    for precision in (0, 1):
+        integ = pkg.Integrator(m, precision=precision)
+        f = integ.eval_rhs(_dev(st.T), _dev(st.p), _dev(st.Y)).cpu().numpy()
+        J = integ.eval_jacobian(_dev(st.T), _dev(st.p), _dev(st.Y)).cpu().numpy()
+        assert np.all(np.isfinite(f)) and np.all(np.isfinite(J))
+        for c in range(st.T.shape[0]):
+            y = np.concatenate([[st.T[c]], st.Y[c]])
+            fr = orc.rhs(M, st.p[c], y)
+            _, _, q = orc.rates(M, st.p[c], y)
+            rho = st.p[c] / (8.31446261815324e7 * st.T[c] * np.sum(st.Y[c] / m.W))
+            gross = np.concatenate([[np.abs(fr[0])], m.W * (nu @ np.abs(q)) / rho])
+            assert np.all(np.abs(f[c] - fr) <= 1e-11 * (np.abs(fr) + gross) + 1e-300), (precision, c)
+            Jr = orc.jac(M, st.p[c], y)
+            row = np.abs(Jr).max(axis=1, keepdims=True) + 1e-300
+            err = np.abs(J[c] - Jr) / (np.abs(Jr) + row)
+            assert err.max() <= 1e-10, (precision, c, err.max())
+
+
 @pytest.mark.parametrize("name", ["h2_10", "c_54"])
 def test_fd_jacobian_vs_oracle(pkg, orc, name):
     """Option jacobian = 1 (forward differences, FP64 form) against the oracle's
