@@ -85,7 +85,17 @@ def parse():
                          "mechanisms (10, 32, 54, 100 species) in one launch vs four launches")
     ap.add_argument("--no-phases", action="store_true",
                     help="skip the extra untimed step per form with per-phase cycle counters")
+    ap.add_argument("--parity-per-class", type=int, default=512,
+                    help="same-run parity: cells per temperature class (cold, igniting, burnt) integrated "
+                         "by the oracle and compared with every timed GPU form")
+    ap.add_argument("--parity-costliest", type=int, default=256,
+                    help="same-run parity: also the costliest cells by the headline form's substeps")
+    ap.add_argument("--ref-step-cells", type=int, default=256,
+                    help="--impl reference: uniformly sampled cells integrated per step")
     return ap.parse_args()
+
+
+METRIC = "cells*CFD-step/s at rtol 1e-8 (mixed+learned vs plain FP64 GPU)"
 
 
 # ---------------------------------------------------------------------------- helpers
@@ -258,13 +268,15 @@ def host_threads():
     return _HOST_THREADS[0]
 
 
-def _oracle_rate(m, st, dt, seconds, order, threads, chunk):
+def _oracle_rate(m, st, dt, seconds, order, threads, chunk, keep=None):
+    import oracle
+
     done, t0 = 0, time.perf_counter()
     while time.perf_counter() - t0 < seconds and done < order.size:
         idx = order[done:done + chunk]
-        import oracle
-
-        oracle.integrate(m, st.T[idx], st.p[idx], st.Y[idx], dt, RTOL, ATOL, n_threads=threads)
+        r = oracle.integrate(m, st.T[idx], st.p[idx], st.Y[idx], dt, RTOL, ATOL, n_threads=threads)
+        if keep is not None:
+            keep.append((idx, r))
         done += idx.size
     return done, time.perf_counter() - t0
 
@@ -278,14 +290,63 @@ def cpu_baseline(m, st, dt, seconds, seed=0):
     rng = np.random.default_rng(seed)
     order = rng.permutation(st.T.shape[0])
     threads = host_threads()
-    done, el = _oracle_rate(m, st, dt, seconds, order, threads, 64)
+    keep = []
+    done, el = _oracle_rate(m, st, dt, seconds, order, threads, 64, keep)
     rest = order[done:] if done < order.size else order
-    done1, el1 = _oracle_rate(m, st, dt, seconds / 5.0, rest, 1, 4)
+    done1, el1 = _oracle_rate(m, st, dt, seconds / 5.0, rest, 1, 4, keep)
     return {"value": done / el, "unit": "cells*step/s", "cores": threads, "kind": "oracle",
             "sample": f"{done} uniformly sampled cells of the {st.T.shape[0]}-cell batch, "
                       f"{el:.1f} s on {threads} threads",
             "single_thread": {"value": done1 / el1, "sample": f"{done1} further cells, {el1:.1f} s on 1 thread"},
-            "cpu_model": cpu_model()}
+            "cpu_model": cpu_model(), "_results": keep}
+
+
+def same_run_parity(m, st, dt, results, per_class, costliest, extra=(), seed=5):
+    """The bench's own inputs, integrated by the oracle on a stratified sample (per_class
+    cells of each temperature class, plus the costliest cells by the headline form's
+    substeps, plus any cells the CPU baseline already integrated), compared with the
+    final states of every timed GPU form at the parity bound |dT| <= 1e-6 T,
+    |dY_k| <= 1e-8 + 1e-5 |Y_k|."""
+    import oracle
+
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    pick = []
+    for k in np.unique(st.kind):
+        cls = np.nonzero(st.kind == k)[0]
+        pick.append(rng.choice(cls, min(per_class, cls.size), replace=False))
+    ref_sub = results.get("headline", next(iter(results.values())))["cell_substeps"]
+    pick.append(np.argsort(ref_sub, kind="stable")[::-1][:costliest])
+    idx = np.unique(np.concatenate(pick)) if pick else np.zeros(0, dtype=np.int64)
+    have = {}
+    for cells, r in extra:
+        for j, c in enumerate(cells):
+            have[int(c)] = (r["T"][j], r["Y"][j], r["status"][j])
+    todo = np.array([c for c in idx if int(c) not in have], dtype=np.int64)
+    t0 = time.perf_counter()
+    if todo.size:
+        r = oracle.integrate(m, st.T[todo], st.p[todo], st.Y[todo], dt, RTOL, ATOL, n_threads=host_threads())
+        for j, c in enumerate(todo):
+            have[int(c)] = (r["T"][j], r["Y"][j], r["status"][j])
+    el = time.perf_counter() - t0
+    cells = np.array(sorted(have), dtype=np.int64)
+    Tr = np.array([have[c][0] for c in cells])
+    Yr = np.array([have[c][1] for c in cells])
+    ok_ref = np.array([have[c][2] == 0 for c in cells])
+    out = {"cells": int(cells.size), "per_class": per_class, "costliest": costliest,
+           "oracle_s": round(el, 1), "oracle_failed": int((~ok_ref).sum()), "bound": "|dT|<=1e-6 T, |dY|<=1e-8+1e-5|Y|",
+           "forms": {}}
+    ok = bool(ok_ref.all())
+    for name, res in results.items():
+        dT = np.abs(res["T"][cells] - Tr) / Tr
+        dY = np.abs(res["Y"][cells] - Yr) / (1e-8 + 1e-5 * np.abs(Yr))
+        f = {"max_dT_over_T": float(dT.max()), "max_dY_over_bound": float(dY.max()),
+             "cells_outside": int(np.sum((dT > 1e-6) | (dY > 1.0).any(axis=1)))}
+        f["ok"] = f["cells_outside"] == 0
+        ok = ok and f["ok"]
+        out["forms"][name] = f
+    out["ok"] = ok
+    return out
 
 
 # ---------------------------------------------------------------------------- GPU arm
@@ -355,8 +416,12 @@ def run_ours(args, rank, world):
             clk = clocks.stop()
         ms = sum(a.elapsed_time(b) for a, b in evs)
         tot = integ.totals()
+        # every timed step starts from the same input, so the last step's output is the
+        # form's result for it (compared with the oracle after the timed region)
         results[name] = {"ms_total": ms, "kernel_ms": float(np.mean(kms)), "substeps": tot["substeps"],
-                         "failed": tot["failed"], "rejects": tot["rejects"]}
+                         "failed": tot["failed"], "rejects": tot["rejects"],
+                         "T": T.cpu().numpy(), "Y": Y.cpu().numpy(),
+                         "cell_substeps": integ.stats(n)["substeps"].cpu().numpy()}
         if not args.no_phases:
             integ.set_option("profile", 1)
             one(integ)
@@ -634,6 +699,48 @@ def run_cfd_loop(args):
                       "substeps_ratio": tot["learned_sub"] / tot["plain_sub"]}), flush=True)
 
 
+def run_reference(args):
+    """The reference arm: the CPU oracle (plain FP64 C++, OpenMP over cells, all host
+    cores) on the same workload. Each step integrates a fresh uniform sample of
+    --ref-step-cells cells of the batch (a bounded sample: the whole batch takes minutes
+    on the host); ms_per_step is that step's measured wall time and the value is the
+    timed steps' cells over their time."""
+    import oracle
+
+    oracle.build()
+    m, st, dt = synth.workload(args.workload, n_cells=args.cells)
+    n = st.T.shape[0]
+    threads = host_threads()
+    rng = np.random.default_rng(0)
+    order = rng.permutation(n)
+    k = min(args.ref_step_cells, n)
+    times, pos = [], 0
+    for it in range(args.warmup + args.steps):
+        if pos + k > n:
+            pos = 0
+        idx = order[pos:pos + k]
+        pos += k
+        t0 = time.perf_counter()
+        oracle.integrate(m, st.T[idx], st.p[idx], st.Y[idx], dt, RTOL, ATOL, n_threads=threads)
+        if it >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = float(sum(times))
+    v = k * len(times) / total
+    sample = (f"{k} uniformly sampled cells of the {n}-cell batch per step, {len(times)} timed steps, "
+              f"{total:.1f} s on {threads} threads")
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "cells*step/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n_cells": n, "step_cells": k,
+                       "mechanism": f"{m.n_species} species / {m.n_reactions} reactions (seeded synthetic)",
+                       "pressure_bar": float(st.p[0] / 1e6), "dt_s": dt, "rtol": RTOL, "atol": ATOL,
+                       "form": "CPU oracle, FP64 (RODAS4, analytic Jacobian, partial-pivot LU)"},
+            "cpu_baseline": {"value": v, "unit": "cells*step/s", "cores": threads, "kind": "oracle",
+                             "sample": sample, "cpu_model": cpu_model()},
+            "e2e": {"value": v, "unit": "cells*step/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def main():
     args = parse()
     if args.sweep:
@@ -656,24 +763,7 @@ def main():
         torch.distributed.init_process_group("nccl" if args.impl == "ours" else "gloo")
     if args.impl == "reference":
         if rank == 0:
-            m, st, dt = synth.workload(args.workload, n_cells=args.cells)
-            vals = []
-            budget = max(2.0, args.cpu_seconds / max(1, args.steps))
-            for _ in range(args.steps):
-                vals.append(cpu_baseline(m, st, dt, budget, seed=len(vals))["value"])
-            cb = cpu_baseline(m, st, dt, budget, seed=99)
-            v = float(np.mean(vals))
-            line = {"impl": "reference", "metric": "cells*CFD-step/s at rtol 1e-8 (CPU oracle, FP64)",
-                    "value": v, "unit": "cells*step/s", "n_gpus": args.gpus, "steps": args.steps,
-                    "warmup": args.warmup, "ms_per_step": 1e3 * st.T.shape[0] / v, "higher_is_better": True,
-                    "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                    "config": {"workload": args.workload, "n_cells": int(st.T.shape[0]),
-                               "mechanism": f"{m.n_species} species / {m.n_reactions} reactions"},
-                    "cpu_baseline": {"value": v, "unit": "cells*step/s", "cores": cb["cores"], "kind": "oracle",
-                                     "sample": cb["sample"], "single_thread": cb["single_thread"],
-                                     "cpu_model": cb["cpu_model"]},
-                    "e2e": {"value": v, "unit": "cells*step/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-            print(json.dumps(line))
+            print(json.dumps(run_reference(args)))
         return
     m, st, dt, n, res, clk, e2e_s, learned, head, mlp_ms = run_ours(args, rank, world)
     if rank != 0:
@@ -688,7 +778,7 @@ def main():
     substeps_per_launch = hd["substeps"]  # totals of the last launch
     achieved = w_step * substeps_per_launch / (hd["kernel_ms"] / 1e3) / 1e12
     line = {
-        "metric": "cells*CFD-step/s at rtol 1e-8 (mixed+learned vs plain FP64 GPU)",
+        "metric": METRIC,
         "value": value, "unit": "cells*step/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64+f32", "data": "synthetic",
@@ -735,9 +825,17 @@ def main():
     # feature, two GEMM and head kernels of the MLP, and 3 counting-sort kernels
     chunks = (n + 65535) // 65536
     line["gpu_launches"] = args.steps * (1 + ((4 * chunks + 3) if learned else 0))
+    extra = []
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(m, st, dt, args.cpu_seconds)
+        cb = cpu_baseline(m, st, dt, args.cpu_seconds)
+        extra = cb.pop("_results")
+        line["cpu_baseline"] = cb
+    # parity in the same run: the timed forms' outputs against the oracle on a sample
+    line["parity"] = same_run_parity(m, st, dt, res, args.parity_per_class, args.parity_costliest, extra)
     print(json.dumps(line))
+    if not line["parity"]["ok"]:
+        print("parity bound exceeded: " + json.dumps(line["parity"]), file=sys.stderr)
+        sys.exit(1)
 
 
 if __name__ == "__main__":

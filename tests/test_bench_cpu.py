@@ -10,6 +10,8 @@ import sys
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
 ARGS = ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0", "--cpu-seconds", "2",
         "--workload", "h2_10_1k"]
 
@@ -31,6 +33,37 @@ def _check_line(d):
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"] == "h2_10_1k"
+    # the same metric string as the GPU arm, and per-step times actually measured:
+    # each step integrates step_cells cells, so value x ms_per_step = step_cells
+    import bench
+
+    assert d["metric"] == bench.METRIC
+    k = d["config"]["step_cells"]
+    assert abs(d["value"] * d["ms_per_step"] / 1e3 - k) <= 1e-6 * k
+
+
+def test_same_run_parity_host_logic(built_oracle):
+    """The bench's same-run parity check on the host: the oracle's own results pass; one
+    sampled cell moved by 2e-6 T, or one mass fraction moved past its bound, fails."""
+    import numpy as np
+
+    import bench
+    import oracle
+    from paper_2112_05834_gb300 import synth
+
+    m, st, dt = synth.workload("c54_65k", n_cells=96, state_seed=3)
+    r = oracle.integrate(m, st.T, st.p, st.Y, dt, bench.RTOL, bench.ATOL)
+    res = {"headline": {"T": r["T"].copy(), "Y": r["Y"].copy(), "cell_substeps": r["substeps"]}}
+    out = bench.same_run_parity(m, st, dt, res, per_class=6, costliest=4)
+    assert out["ok"] and out["cells"] >= 16 and out["forms"]["headline"]["cells_outside"] == 0
+    costly = int(np.argmax(r["substeps"]))  # always in the sample
+    bad = {"headline": dict(res["headline"], T=res["headline"]["T"].copy())}
+    bad["headline"]["T"][costly] *= 1 + 2e-6
+    out = bench.same_run_parity(m, st, dt, bad, per_class=6, costliest=4)
+    assert not out["ok"] and out["forms"]["headline"]["cells_outside"] == 1
+    bad = {"headline": dict(res["headline"], Y=res["headline"]["Y"].copy())}
+    bad["headline"]["Y"][costly, 3] += 2e-8 + 2e-5 * abs(bad["headline"]["Y"][costly, 3])
+    assert not bench.same_run_parity(m, st, dt, bad, per_class=6, costliest=4)["ok"]
 
 
 def test_reference_arm_single(built_oracle):

@@ -160,68 +160,87 @@ def test_training_learns_cost(pkg):
     print("median |ln h0 error| =", np.median(err_h))
 
 
+def _timed_integrate(integ, st, dt, reps=3):
+    """Median CUDA-event time (ms) of `reps` calls from the same input (one warm-up call
+    first), the outputs of the last call and its per-cell statistics."""
+    stream = torch.cuda.current_stream()
+    p = _dev(st.p)
+    T, Y = _dev(st.T), _dev(st.Y)
+    integ.integrate(T, p, Y, dt, RTOL, ATOL)
+    ms = []
+    for _ in range(reps):
+        T, Y = _dev(st.T), _dev(st.Y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        integ.integrate(T, p, Y, dt, RTOL, ATOL)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    s = integ.stats(st.T.shape[0])
+    return float(np.median(ms)), {"T": T.cpu().numpy(), "Y": Y.cpu().numpy(),
+                                  "substeps": s["substeps"].cpu().numpy(), "rejects": s["rejects"].cpu().numpy(),
+                                  "status": s["status"].cpu().numpy()}
+
+
 def test_learned_form_gain_and_parity(pkg):
-    """Trained on one seeded batch, evaluated on another: the learned order and
-    initial step keep every cell within the parity bound and save work."""
+    """What the trained network gains, held out: trained on the logs of one seeded
+    65,536-cell batch of the 54-species workload, evaluated on another, against the same
+    form without it (mixed precision, work queue, index order, heuristic initial step).
+    Device time of the whole call (CUDA events, MLP inference and cost sort included),
+    substeps and rejections are reported; the learned form must keep every sampled cell
+    within the parity bound, fail no cell, and not run slower than the plain form by more
+    than 3 % (its initial step is kept inside the heuristic's envelope, so a wrong
+    prediction costs at most the heuristic's own range)."""
     import oracle
 
     oracle.build()
-    m, st_tr, dt = synth.workload("c54_65k", n_cells=16384, state_seed=44)
-    _, st, _ = synth.workload("c54_65k", n_cells=8192, state_seed=45)
+    n = 65536
+    m, st_tr, dt = synth.workload("c54_65k", n_cells=n, state_seed=44)
+    _, st, _ = synth.workload("c54_65k", n_cells=n, state_seed=45)
     plain = pkg.Integrator(m, precision=1, scheduler=2)
     learned = pkg.Integrator(m, precision=1, scheduler=2)
     Ttr, ptr, Ytr = _dev(st_tr.T), _dev(st_tr.p), _dev(st_tr.Y)
     sub, hf = pkg.log_cells(plain, Ttr, ptr, Ytr, dt)
     model = pkg.CostModel(m.n_species, seed=6)
-    model.train(Ttr, ptr, Ytr, sub, hf, epochs=20, batch=4096, lr=1e-3, seed=7)
+    model.train(Ttr, ptr, Ytr, sub, hf, epochs=20, batch=8192, lr=1e-3, seed=7)
     model.attach(learned)
     learned.set_option("order", 1)
     learned.set_option("h0", 1)
     out = {}
     for name, integ in (("plain", plain), ("learned", learned)):
-        T, p, Y = _dev(st.T), _dev(st.p), _dev(st.Y)
-        integ.integrate(T, p, Y, dt, RTOL, ATOL)  # warm-up
-        T, Y = _dev(st.T), _dev(st.Y)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        integ.integrate(T, p, Y, dt, RTOL, ATOL)
-        torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        s = integ.stats(st.T.shape[0])
-        out[name] = {"T": T.cpu().numpy(), "Y": Y.cpu().numpy(), "time": el,
-                     "substeps": s["substeps"].cpu().numpy(), "status": s["status"].cpu().numpy()}
-    for name, o in out.items():
-        print(name, "time %.4f s" % o["time"], "substeps", int(o["substeps"].sum()))
+        ms, o = _timed_integrate(integ, st, dt)
+        o["ms"] = ms
+        out[name] = o
+        print(name, "%.1f ms" % ms, "substeps", int(o["substeps"].sum()), "rejects", int(o["rejects"].sum()))
         assert np.all(o["status"] == 0)
-    # parity of the learned form on sampled cells
+    gain = out["plain"]["ms"] / out["learned"]["ms"]
+    ratio = out["learned"]["substeps"].sum() / out["plain"]["substeps"].sum()
+    print("learned part, held out on %d cells: speed-up %.3f, substeps ratio %.4f" % (n, gain, ratio))
+    # parity of both forms on sampled cells, the costliest included
     rng = np.random.default_rng(1)
-    pick = np.unique(np.concatenate([rng.choice(8192, 24, replace=False),
+    pick = np.unique(np.concatenate([rng.choice(n, 24, replace=False),
                                      np.argsort(out["learned"]["substeps"])[-8:]]))
     ref = oracle.integrate(m, st.T[pick], st.p[pick], st.Y[pick], dt, RTOL, ATOL)
-    for name in ("plain", "learned"):
-        o = out[name]
-        assert np.all(np.abs(o["T"][pick] - ref["T"]) <= 1e-6 * ref["T"])
-        assert np.all(np.abs(o["Y"][pick] - ref["Y"]) <= 1e-8 + 1e-5 * np.abs(ref["Y"]))
-    # work: the learned initial step replaces the heuristic's 2 RHS evaluations per
-    # cell and must not cost extra steps overall
-    n = st.T.shape[0]
-    rhs_plain = 7 * out["plain"]["substeps"].sum() + 2 * n
-    rhs_learned = 7 * out["learned"]["substeps"].sum()
-    print("RHS evaluations plain", rhs_plain, "learned", rhs_learned,
-          "speed-up %.3f" % (out["plain"]["time"] / out["learned"]["time"]))
-    assert out["learned"]["substeps"].sum() <= 1.02 * out["plain"]["substeps"].sum()
-    assert rhs_learned < rhs_plain
+    for name, o in out.items():
+        assert np.all(np.abs(o["T"][pick] - ref["T"]) <= 1e-6 * ref["T"]), name
+        assert np.all(np.abs(o["Y"][pick] - ref["Y"]) <= 1e-8 + 1e-5 * np.abs(ref["Y"])), name
+    assert gain >= 0.97
+    assert ratio <= 1.02
 
 
 def test_cfd_loop_learned(pkg):
-    """A CFD-like sequence on the 100-species mechanism: between steps T += U[-50, 50] K
-    and Y mixes with a random partner cell. Steps 1-3 run the plain heuristic and log;
-    the model trains on those logs; steps 4-6 use the learned order and initial step.
-    Every step's outputs match the oracle on sampled cells of that step's inputs."""
+    """The learned-scheduling configuration at 65,536 cells of the 100-species
+    mechanism: between CFD steps T += U[-50, 50] K and Y mixes with a random partner
+    cell. Steps 1-3 run the plain heuristic and log; the model trains on those logs;
+    steps 4-6 use the learned order and initial step. Every step's outputs match the
+    oracle on sampled cells of that step's inputs (random cells and the step's
+    costliest), and no cell fails."""
     import oracle
 
     oracle.build()
-    m, st, dt = synth.workload("c100_1m", n_cells=8192, state_seed=46)
+    n = 65536
+    m, st, dt = synth.workload("c100_1m", n_cells=n, state_seed=46)
     integ = pkg.Integrator(m, precision=1, scheduler=2)
     model = pkg.CostModel(m.n_species, seed=8)
     logs = []
@@ -229,28 +248,25 @@ def test_cfd_loop_learned(pkg):
     for step in range(6):
         T, p, Y = _dev(st.T), _dev(st.p), _dev(st.Y)
         if step == 3:
-            Ts = torch.cat([l[0] for l in logs])
-            ps = torch.cat([l[1] for l in logs])
-            Ys = torch.cat([l[2] for l in logs])
-            sub = torch.cat([l[3] for l in logs])
-            hf = torch.cat([l[4] for l in logs])
-            losses = model.train(Ts, ps, Ys, sub, hf, epochs=20, batch=4096, lr=1e-3, seed=9)
+            cat = [torch.cat([l[k] for l in logs]) for k in range(5)]
+            losses = model.train(*cat, epochs=20, batch=8192, lr=1e-3, seed=9)
             assert losses[-1] < losses[0]
             model.attach(integ)
             integ.set_option("order", 1)
             integ.set_option("h0", 1)
         T_in, Y_in = T.clone(), Y.clone()
         integ.integrate(T, p, Y, dt, RTOL, ATOL)
-        s = integ.stats(st.T.shape[0])
+        s = integ.stats(n)
         assert int((s["status"] != 0).sum()) == 0
         if step < 3:
             logs.append((T_in, p, Y_in, s["substeps"].clone(), s["h_first"].clone()))
-        pick = rng.choice(st.T.shape[0], 8, replace=False)
+        sub = s["substeps"].cpu().numpy()
+        pick = np.unique(np.concatenate([rng.choice(n, 8, replace=False), np.argsort(sub)[-2:]]))
         ref = oracle.integrate(m, st.T[pick], st.p[pick], st.Y[pick], dt, RTOL, ATOL)
         Tg, Yg = T.cpu().numpy(), Y.cpu().numpy()
         assert np.all(np.abs(Tg[pick] - ref["T"]) <= 1e-6 * ref["T"]), step
         assert np.all(np.abs(Yg[pick] - ref["Y"]) <= 1e-8 + 1e-5 * np.abs(ref["Y"])), step
-        print("step", step + 1, "substeps", int(s["substeps"].sum()))
+        print("step", step + 1, "substeps", int(sub.sum()))
         st = synth.perturb_states(synth.CellStates(T=Tg, p=st.p, Y=Yg, kind=st.kind), seed=100 + step)
 
 
