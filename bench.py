@@ -61,9 +61,12 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU baseline time budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--forms", default="plain_fp64,mixed,headline",
+    ap.add_argument("--forms", default="plain_fp64,mixed,w_method,headline",
                     help="plain_fp64: FP64, one CTA per cell; mixed: mixed precision + work queue; "
+                         "w_method: the ROS34PW2 W-method with the Jacobian assembled in FP32 (+ queue); "
                          "headline: mixed + queue + learned order/h0")
+    ap.add_argument("--compare-steps", type=int, default=3,
+                    help="timed steps of each comparison form (the headline form takes --steps)")
     ap.add_argument("--sweep", action="store_true",
                     help="per-cell time vs absolute tolerance for the FP64 form's classical variants "
                          "(forward-difference Jacobian, elimination without pivoting); one JSON line each")
@@ -370,8 +373,9 @@ def run_ours(args, rank, world):
     forms = {}
     plain = pkg.Integrator(m, precision=0, scheduler=0)
     mixed = pkg.Integrator(m, precision=1, scheduler=2, ir_sweeps=1)
+    wmeth = pkg.Integrator(m, precision=2, scheduler=2, ir_sweeps=1, method=1)
     head = pkg.Integrator(m, precision=1, scheduler=2, ir_sweeps=1)
-    for integ in (plain, mixed, head):
+    for integ in (plain, mixed, wmeth, head):
         integ.set_option("time_kernel", 1)  # CUDA events around the integration kernel
     learned = False
     if not args.no_learned and hasattr(pkg, "train_cost_model"):
@@ -381,6 +385,8 @@ def run_ours(args, rank, world):
         forms["plain_fp64"] = plain
     if "mixed" in want:
         forms["mixed"] = mixed
+    if "w_method" in want:
+        forms["w_method"] = wmeth
     if "headline" in want:
         forms["headline"] = head
 
@@ -399,7 +405,10 @@ def run_ours(args, rank, world):
     clocks = ClockSampler(dev.index)
     clk = None
     for name, integ in forms.items():
-        for _ in range(args.warmup):
+        # the headline form is the benchmark (W warm-up, K timed steps); the comparison
+        # forms are timed on fewer steps from the same input
+        steps = args.steps if name == "headline" else min(args.steps, args.compare_steps)
+        for _ in range(args.warmup if name == "headline" else min(args.warmup, 1)):
             one(integ)
         torch.cuda.synchronize()
         if world > 1:
@@ -408,7 +417,7 @@ def run_ours(args, rank, world):
         if name == "headline":
             clocks.start()
         evs, kms = [], []
-        for _ in range(args.steps):
+        for _ in range(steps):
             evs.append(one(integ))
             kms.append(integ.kernel_ms())  # waits for this step's integration kernel
         torch.cuda.synchronize()
@@ -418,7 +427,7 @@ def run_ours(args, rank, world):
         tot = integ.totals()
         # every timed step starts from the same input, so the last step's output is the
         # form's result for it (compared with the oracle after the timed region)
-        results[name] = {"ms_total": ms, "kernel_ms": float(np.mean(kms)), "substeps": tot["substeps"],
+        results[name] = {"ms_total": ms, "steps": steps, "kernel_ms": float(np.mean(kms)), "substeps": tot["substeps"],
                          "failed": tot["failed"], "rejects": tot["rejects"],
                          "T": T.cpu().numpy(), "Y": Y.cpu().numpy(),
                          "cell_substeps": integ.stats(n)["substeps"].cpu().numpy()}
@@ -481,7 +490,9 @@ def run_sweep(args):
     variants = [("fd_jacobian+no_pivoting", dict(precision=0, jacobian=1, pivoting=0)),
                 ("analytic+no_pivoting", dict(precision=0, jacobian=0, pivoting=0)),
                 ("analytic+lu", dict(precision=0, jacobian=0, pivoting=1)),
-                ("analytic+mixed", dict(precision=1))]
+                ("analytic+mixed", dict(precision=1)),
+                ("rodas4+fp32_assembly", dict(precision=2)),
+                ("w_method+fp32_assembly", dict(precision=2, method=1))]
     for atol in (1e-6, 1e-8, 1e-10, 1e-12):
         for name, opt in variants:
             integ = pkg.Integrator(m, scheduler=2, time_kernel=1, **opt)
@@ -801,10 +812,10 @@ def main():
     }
     if "plain_fp64" in res:
         pl = res["plain_fp64"]
-        pv = n * args.steps / (pl["ms_total"] / 1e3)
+        pv = n * pl["steps"] / (pl["ms_total"] / 1e3)
         w0 = algorithmic_fp64_flops_per_step(m, 0, 0)
         a0 = w0 * pl["substeps"] / (pl["kernel_ms"] / 1e3) / 1e12
-        line["plain_fp64"] = {"value": pv, "ms_per_step": pl["ms_total"] / args.steps, "kernel_ms": pl["kernel_ms"],
+        line["plain_fp64"] = {"value": pv, "ms_per_step": pl["ms_total"] / pl["steps"], "kernel_ms": pl["kernel_ms"],
                               "substeps_per_step": pl["substeps"],
                               "roofline_fp64_frac": a0 / FP64_PEAK_TFLOPS, "achieved_tflops": a0}
         if "phases" in pl:
@@ -812,12 +823,24 @@ def main():
         line["speedup_vs_plain_fp64"] = value / pv
     if "mixed" in res:
         mx = res["mixed"]
-        mv = n * args.steps / (mx["ms_total"] / 1e3)
-        line["mixed_without_learned"] = {"value": mv, "ms_per_step": mx["ms_total"] / args.steps,
+        mv = n * mx["steps"] / (mx["ms_total"] / 1e3)
+        line["mixed_without_learned"] = {"value": mv, "ms_per_step": mx["ms_total"] / mx["steps"],
                                          "kernel_ms": mx["kernel_ms"], "substeps_per_step": mx["substeps"]}
         if "phases" in mx:
             line["mixed_without_learned"]["phase_share"] = mx["phases"]
         line["learned_gain"] = value / mv
+    if "w_method" in res:
+        wm = res["w_method"]
+        wv = n * wm["steps"] / (wm["ms_total"] / 1e3)
+        line["w_method_fp32_assembly"] = {
+            "value": wv, "ms_per_step": wm["ms_total"] / wm["steps"], "kernel_ms": wm["kernel_ms"],
+            "substeps_per_step": wm["substeps"], "rejects_per_step": wm["rejects"], "failed_cells": wm["failed"],
+            "headline_substeps_per_step": hd["substeps"], "headline_rejects_per_step": hd["rejects"],
+            "speed_vs_headline": wv / value,
+            "form": "ROS34PW2 W-method, Jacobian assembled in FP32, FP32 Gauss-Jordan, FP64 refinement "
+                    "against the FP32 matrix, queue"}
+        if "phases" in wm:
+            line["w_method_fp32_assembly"]["phase_share"] = wm["phases"]
     if "phases" in hd:
         line["phase_share"] = hd["phases"]
         line["phase_roofline"] = phase_rooflines(m, hd, n, mlp_ms)

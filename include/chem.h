@@ -231,6 +231,13 @@ chem_status chem_integrate_jobs(const chem_job* jobs, int32_t n_jobs, double dt,
  *   "job_launch"  chem_integrate_jobs only (read from jobs[0].h): 0 = one kernel
  *                 launch for all jobs (default); 1 = one launch per job on
  *                 concurrent streams, each with its own handle's options
+ *   "method"      0 = RODAS4 (default; order 4, embedded order 3, for the exact
+ *                 Jacobian); 1 = ROS34PW2 (Rang & Angermann 2005: a W-method, order
+ *                 3 for ANY approximation W of the Jacobian, embedded order 2). The
+ *                 W-method is the consistent partner of precision 2: the FP32-
+ *                 assembled matrix is a W, and the order survives its rounding,
+ *                 where RODAS4 loses order (Methodology, "Analytical Jacobian and
+ *                 improved ODE solution", leaves the ODE scheme open)
  *   "time_kernel" 1 = record CUDA events on the stream around each integration
  *                 kernel launch (chem_get_kernel_ms); chem_integrate_noalloc
  *                 does not record them
@@ -393,6 +400,13 @@ chem_status chem_eval_math(int32_t op, int64_t n, const double* x, double* y, vo
  * needs no GPU.
  */
 void chem_rosenbrock_tableau(double* gamma, double* a, double* c, double* m, double* e);
+
+/*
+ * As chem_rosenbrock_tableau for option "method" = `method` (0 RODAS4,
+ * 1 ROS34PW2); entries beyond the method's stage count are zero. Returns the
+ * number of stages, or -1 for an unknown method. Host only; needs no GPU.
+ */
+int32_t chem_method_tableau(int32_t method, double* gamma, double* a, double* c, double* m, double* e);
 
 #ifdef __cplusplus
 }

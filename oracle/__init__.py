@@ -7,8 +7,8 @@ it, and it imports nothing from the GPU path (only the seeded input generator
 
 ``oracle.cpp`` is the plain C++ restatement of the method (thermo, rates, RHS,
 analytic / finite-difference / complex-step Jacobians, dense partial-pivot LU,
-RODAS4 in its original form, starting step, step control, temperature
-recovery). ``equilibrium.py`` (constant-enthalpy Gibbs minimisation) and
+RODAS4 and the ROS34PW2 W-method in their original form, starting step, step
+control, temperature recovery). ``equilibrium.py`` (constant-enthalpy Gibbs minimisation) and
 ``mlp_ref.py`` (FP64 MLP forward/backward) are further oracle-side references.
 
 Every function here is pinned by the ``-m "not gpu"`` tests to something other
@@ -75,7 +75,10 @@ def _load():
                 "oracle_h0": (D, [P, D, P, D, D, D]),
                 "oracle_enthalpy_mass": (D, [P, D, P]),
                 "oracle_recover_T": (D, [P, P, D, D]),
-                "oracle_integrate": (I64, [P, I64, P, P, P, D, D, D, I32, P, P, P, P, P, P, I32]),
+                "oracle_integrate": (I64, [P, I64, P, P, P, D, D, D, I32, P, P, P, P, P, P, I32, I32]),
+                "oracle_tableau_m": (C.c_int, [C.c_int, P, P, P, P, P]),
+                "oracle_row_step": (C.c_int, [P, D, P, D, P, P, C.c_int, P]),
+                "oracle_h0_m": (D, [P, D, P, D, D, D, C.c_int]),
                 "oracle_max_threads": (C.c_int, []),
             }
             for name, (res, args) in sig.items():
@@ -195,6 +198,30 @@ def tableau():
     return alpha, gam, b, bhat
 
 
+METHODS = {"rodas4": 0, "ros34pw2": 1}
+
+
+def tableau_of(method):
+    """(alpha, gamma, b, bhat, q) of a method ("rodas4" or "ros34pw2"), trimmed to its stages."""
+    alpha, gam = np.zeros((6, 6)), np.zeros((6, 6))
+    b, bhat, q = np.zeros(6), np.zeros(6), C.c_double()
+    s = _load().oracle_tableau_m(METHODS[method], _ptr(alpha), _ptr(gam), _ptr(b), _ptr(bhat), C.byref(q))
+    return alpha[:s, :s], gam[:s, :s], b[:s], bhat[:s], q.value
+
+
+def row_step(m, p, y0, h, method="rodas4", E=None):
+    """One step with W = J(y0) + E (E: an optional fixed perturbation of the Jacobian)."""
+    m = as_mech(m)
+    y0 = _f64(y0)
+    y1, yh = np.zeros(m.n), np.zeros(m.n)
+    Ea = None if E is None else _f64(E, (m.n, m.n))
+    info = _load().oracle_row_step(m.ref, float(p), _ptr(y0), float(h), _ptr(y1), _ptr(yh), METHODS[method],
+                                   _ptr(Ea))
+    if info:
+        raise RuntimeError("singular iteration matrix")
+    return y1, yh
+
+
 def rodas_step(m, p, y0, h):
     m = as_mech(m)
     y0 = _f64(y0)
@@ -205,9 +232,10 @@ def rodas_step(m, p, y0, h):
     return y1, yh
 
 
-def h0(m, p, y0, dt, rtol, atol):
+def h0(m, p, y0, dt, rtol, atol, method="rodas4"):
     m = as_mech(m)
-    return _load().oracle_h0(m.ref, float(p), _ptr(_f64(y0)), float(dt), float(rtol), float(atol))
+    return _load().oracle_h0_m(m.ref, float(p), _ptr(_f64(y0)), float(dt), float(rtol), float(atol),
+                               METHODS[method])
 
 
 def enthalpy_mass(m, T, Y):
@@ -224,8 +252,10 @@ def max_threads() -> int:
     return int(_load().oracle_max_threads())
 
 
-def integrate(m, T, p, Y, dt, rtol=1e-8, atol=1e-12, max_steps=100000, h0=None, n_threads=0):
-    """Integrate a batch of cells over dt. Returns a dict of result arrays (inputs untouched)."""
+def integrate(m, T, p, Y, dt, rtol=1e-8, atol=1e-12, max_steps=100000, h0=None, n_threads=0,
+              method="rodas4"):
+    """Integrate a batch of cells over dt with RODAS4 or the ROS34PW2 W-method. Returns a
+    dict of result arrays (inputs untouched)."""
     m = as_mech(m)
     T = np.array(T, dtype=np.float64)
     p = _f64(p)
@@ -241,6 +271,6 @@ def integrate(m, T, p, Y, dt, rtol=1e-8, atol=1e-12, max_steps=100000, h0=None, 
     h0a = None if h0 is None else _f64(h0)
     failed = _load().oracle_integrate(
         m.ref, n, _ptr(T), _ptr(p), _ptr(Y), float(dt), float(rtol), float(atol), int(max_steps),
-        _ptr(h0a), _ptr(sub), _ptr(rej), _ptr(hf), _ptr(st), _ptr(Tode), int(n_threads))
+        _ptr(h0a), _ptr(sub), _ptr(rej), _ptr(hf), _ptr(st), _ptr(Tode), int(n_threads), METHODS[method])
     return {"T": T, "Y": Y, "substeps": sub, "rejects": rej, "h_first": hf, "status": st,
             "T_ode": Tode, "failed": int(failed)}

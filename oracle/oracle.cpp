@@ -442,20 +442,26 @@ void lu_solve(int n, const double* a, const int32_t* piv, double* x) {
   }
 }
 
-// ---------------------------------------------------------------- RODAS4 tableau
-// Hairer & Wanner, Solving ODEs II, Sec. VI.4: the published RODAS coefficients
+// ---------------------------------------------------------------- tableaus
+// A Rosenbrock method in its original form (Hairer & Wanner II, Sec. IV.7, Eq. 7.1):
+//   (I - h gamma W) k_i = h f(y0 + sum_{j<i} alpha_ij k_j) + h W sum_{j<i} gamma_ij k_j,
+//   y1 = y0 + sum b_i k_i, embedded yhat = y0 + sum bhat_i k_i,
+// with W the Jacobian (Rosenbrock / ROW methods) or any approximation of it (W-methods).
+// q = order of the embedded solution + 1, the exponent of the step-size control.
+struct Tableau {
+  int s;
+  double alpha[6][6];
+  double gam[6][6];  // Gamma, lower triangular including the diagonal gamma
+  double b[6], bhat[6];
+  double gamma, q;
+};
+
+// RODAS4, Hairer & Wanner, Solving ODEs II, Sec. VI.4: the published coefficients
 // in the transformed variables u_i = sum_j gamma_ij k_j (Sec. IV.7, Eq. 7.3):
 // a = alpha Gamma^-1, c = diag(1/gamma) - Gamma^-1, m = b^T Gamma^-1. The
 // original (alpha, gamma, b, bhat) form the oracle integrates with is
 // recovered here by inverting that transformation.
-struct Tableau {
-  double alpha[6][6];
-  double gam[6][6];  // Gamma, lower triangular including the diagonal gamma
-  double b[6], bhat[6];
-  double gamma;
-};
-
-Tableau make_tableau() {
+Tableau make_rodas4() {
   const double g = 0.25;
   double A[6][6] = {{0}};
   double Cc[6][6] = {{0}};
@@ -500,8 +506,10 @@ Tableau make_tableau() {
       G[i][j] = s / Gi[i][i];
     }
   }
-  Tableau t;
+  Tableau t{};
+  t.s = 6;
   t.gamma = g;
+  t.q = 4.0;
   for (int i = 0; i < 6; ++i) {
     for (int j = 0; j < 6; ++j) {
       double s = 0.0;
@@ -522,24 +530,61 @@ Tableau make_tableau() {
   return t;
 }
 
-const Tableau& tableau() {
-  static const Tableau t = make_tableau();
+// ROS34PW2, J. Rang and L. Angermann, "New Rosenbrock W-methods of order 3 for
+// partial differential algebraic equations of index 1", BIT 45 (2005): 4 stages,
+// order 3 for ANY W (a W-method), embedded order 2, stiffly accurate, L-stable.
+// The published coefficients in the original form.
+Tableau make_ros34pw2() {
+  const double g = 4.3586652150845900e-01;
+  Tableau t{};
+  t.s = 4;
+  t.gamma = g;
+  t.q = 3.0;
+  t.alpha[1][0] = 8.7173304301691801e-01;
+  t.alpha[2][0] = 8.4457060015369423e-01;
+  t.alpha[2][1] = -1.1299064236484185e-01;
+  t.alpha[3][2] = 1.0;
+  t.gam[1][0] = -8.7173304301691801e-01;
+  t.gam[2][0] = -9.0338057013044082e-01;
+  t.gam[2][1] = 5.4180672388095326e-02;
+  t.gam[3][0] = 2.4212380706095346e-01;
+  t.gam[3][1] = -1.2232505839045147e+00;
+  t.gam[3][2] = 5.4526025533510214e-01;
+  for (int i = 0; i < 4; ++i) t.gam[i][i] = g;
+  const double b[4] = {2.4212380706095346e-01, -1.2232505839045147e+00, 1.5452602553351020e+00, g};
+  const double bh[4] = {3.7810903145819369e-01, -9.6042292212423178e-02, 0.5, 2.1793326075422950e-01};
+  for (int i = 0; i < 4; ++i) {
+    t.b[i] = b[i];
+    t.bhat[i] = bh[i];
+  }
   return t;
 }
 
-// ---------------------------------------------------------------- one RODAS4 step
-// Original form: (I - h gamma J) k_i = h f(y0 + sum_{j<i} alpha_ij k_j) + h J sum_{j<i} gamma_ij k_j.
+enum { METHOD_RODAS4 = 0, METHOD_ROS34PW2 = 1 };
+
+const Tableau& tableau(int method = METHOD_RODAS4) {
+  static const Tableau t0 = make_rodas4();
+  static const Tableau t1 = make_ros34pw2();
+  return method == METHOD_ROS34PW2 ? t1 : t0;
+}
+
+// ---------------------------------------------------------------- one Rosenbrock step
+// Original form (see Tableau) with W = the analytic Jacobian at y0, plus E when E is
+// given (a fixed perturbation: the W-method property is that the order survives it).
 // Returns 0 on success, nonzero for a singular iteration matrix.
-int rodas_step(const OMech& m, double p, const double* y0, double h, double* y1, double* yhat) {
-  const Tableau& tb = tableau();
-  const int n = m.K + 1;
-  std::vector<double> J((size_t)n * n), M((size_t)n * n), kst((size_t)6 * n), yi(n), fi(n), v(n), Jv(n);
+int row_step(const OMech& m, double p, const double* y0, double h, double* y1, double* yhat, int method,
+             const double* E) {
+  const Tableau& tb = tableau(method);
+  const int n = m.K + 1, S = tb.s;
+  std::vector<double> J((size_t)n * n), M((size_t)n * n), kst((size_t)S * n), yi(n), fi(n), v(n), Jv(n);
   std::vector<int32_t> piv(n);
   jac_analytic(m, p, y0, J.data(), nullptr);
+  if (E)
+    for (size_t e = 0; e < (size_t)n * n; ++e) J[e] += E[e];
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) M[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) - h * tb.gamma * J[(size_t)i * n + j];
   if (lu_factor(n, M.data(), piv.data())) return 1;
-  for (int s = 0; s < 6; ++s) {
+  for (int s = 0; s < S; ++s) {
     for (int l = 0; l < n; ++l) {
       double a = y0[l], g = 0.0;
       for (int j = 0; j < s; ++j) {
@@ -561,7 +606,7 @@ int rodas_step(const OMech& m, double p, const double* y0, double h, double* y1,
   }
   for (int i = 0; i < n; ++i) {
     double a = y0[i], ah = y0[i];
-    for (int s = 0; s < 6; ++s) {
+    for (int s = 0; s < S; ++s) {
       a += tb.b[s] * kst[(size_t)s * n + i];
       ah += tb.bhat[s] * kst[(size_t)s * n + i];
     }
@@ -569,6 +614,10 @@ int rodas_step(const OMech& m, double p, const double* y0, double h, double* y1,
     yhat[i] = ah;
   }
   return 0;
+}
+
+int rodas_step(const OMech& m, double p, const double* y0, double h, double* y1, double* yhat) {
+  return row_step(m, p, y0, h, y1, yhat, METHOD_RODAS4, nullptr);
 }
 
 double wrms(int n, const double* e, const double* ya, const double* yb, double rtol, double atol) {
@@ -582,9 +631,11 @@ double wrms(int n, const double* e, const double* ya, const double* yb, double r
 }
 
 // Hairer-Wanner starting step size (Solving ODEs I, Sec. II.4) in the WRMS norm
-// with scale atol + rtol |y0_i|; exponent 1/4 (embedded order 3, plus one);
-// clamped to dt. A vanishing derivative selects the whole interval.
-double h0_estimate(const OMech& m, double p, const double* y0, double dt, double rtol, double atol) {
+// with scale atol + rtol |y0_i|; exponent 1/q (embedded order plus one: 1/4 for
+// RODAS4, 1/3 for ROS34PW2); clamped to dt. A vanishing derivative selects the
+// whole interval.
+double h0_estimate(const OMech& m, double p, const double* y0, double dt, double rtol, double atol,
+                   double q = 4.0) {
   const int n = m.K + 1;
   std::vector<double> f0(n), f1(n), y1(n), d(n);
   rhs(m, p, y0, f0.data());
@@ -597,7 +648,7 @@ double h0_estimate(const OMech& m, double p, const double* y0, double dt, double
   for (int i = 0; i < n; ++i) d[i] = f1[i] - f0[i];
   double d2 = wrms(n, d.data(), y0, y0, rtol, atol) / ha;
   double mx = std::max(d1, d2);
-  double hb = (mx > 1e-300) ? std::pow(0.01 / mx, 0.25) : dt;
+  double hb = (mx > 1e-300) ? std::pow(0.01 / mx, 1.0 / q) : dt;
   return std::min(std::min(100.0 * ha, hb), dt);
 }
 
@@ -641,13 +692,14 @@ struct CellResult {
 
 // Adaptive integration of one cell over [0, dt]; y in/out (last accepted state).
 CellResult integrate_cell(const OMech& m, double p, double* y, double dt, double rtol, double atol,
-                          int max_steps, double h_init) {
+                          int max_steps, double h_init, int method) {
   const int n = m.K + 1;
+  const double q = tableau(method).q;
   const double facmin = 0.2, facmax = 5.0, safety = 0.9, h_min = 1e-20;
   CellResult r{0, 0, ST_OK, 0.0, y[0]};
   std::vector<double> y1(n), yh(n), e(n);
   const double h_target = enthalpy_mass(m, y[0], y + 1);
-  double h = (h_init > 0.0) ? std::min(h_init, dt) : h0_estimate(m, p, y, dt, rtol, atol);
+  double h = (h_init > 0.0) ? std::min(h_init, dt) : h0_estimate(m, p, y, dt, rtol, atol, q);
   double t = 0.0;
   bool after_reject = false;
   while (true) {
@@ -655,7 +707,7 @@ CellResult integrate_cell(const OMech& m, double p, double* y, double dt, double
     if (r.substeps >= max_steps) { r.status = ST_MAX_STEPS; break; }
     if (!(h >= h_min)) { r.status = ST_H_UNDERFLOW; break; }
     if (t + h > dt) h = dt - t;
-    int bad = rodas_step(m, p, y, h, y1.data(), yh.data());
+    int bad = row_step(m, p, y, h, y1.data(), yh.data(), method, nullptr);
     r.substeps++;
     double err;
     bool finite = !bad;
@@ -671,7 +723,7 @@ CellResult integrate_cell(const OMech& m, double p, double* y, double dt, double
       h *= facmin;
       continue;
     }
-    double fac = (err > 0.0) ? safety * std::pow(err, -0.25) : facmax;
+    double fac = (err > 0.0) ? safety * std::pow(err, -1.0 / q) : facmax;
     if (err <= 1.0) {
       t += h;
       for (int i = 0; i < n; ++i) y[i] = y1[i];
@@ -755,9 +807,11 @@ void oracle_jac_cstep(const OMech* m, double p, const double* y, double* J) {
 int oracle_lu_factor(int n, double* a, int32_t* piv) { return lu_factor(n, a, piv); }
 void oracle_lu_solve(int n, const double* a, const int32_t* piv, double* x) { lu_solve(n, a, piv, x); }
 
-// alpha[36], gamma[36] (row-major 6x6, Gamma including its diagonal), b[6], bhat[6].
-void oracle_tableau(double* alpha, double* gam, double* b, double* bhat) {
-  const Tableau& t = tableau();
+// Tableau of `method` (0 RODAS4, 1 ROS34PW2): alpha[36], gamma[36] (row-major 6x6,
+// Gamma including its diagonal, zero beyond the stage count), b[6], bhat[6];
+// returns the number of stages.
+int oracle_tableau_m(int method, double* alpha, double* gam, double* b, double* bhat, double* q) {
+  const Tableau& t = tableau(method);
   for (int i = 0; i < 6; ++i)
     for (int j = 0; j < 6; ++j) {
       alpha[6 * i + j] = t.alpha[i][j];
@@ -767,14 +821,30 @@ void oracle_tableau(double* alpha, double* gam, double* b, double* bhat) {
     b[i] = t.b[i];
     bhat[i] = t.bhat[i];
   }
+  if (q) *q = t.q;
+  return t.s;
+}
+
+void oracle_tableau(double* alpha, double* gam, double* b, double* bhat) {
+  oracle_tableau_m(METHOD_RODAS4, alpha, gam, b, bhat, nullptr);
 }
 
 int oracle_rodas_step(const OMech* m, double p, const double* y0, double h, double* y1, double* yhat) {
   return rodas_step(*m, p, y0, h, y1, yhat);
 }
 
+// One step of `method` with W = J(y0) + E (E nullable: the exact Jacobian).
+int oracle_row_step(const OMech* m, double p, const double* y0, double h, double* y1, double* yhat, int method,
+                    const double* E) {
+  return row_step(*m, p, y0, h, y1, yhat, method, E);
+}
+
 double oracle_h0(const OMech* m, double p, const double* y0, double dt, double rtol, double atol) {
   return h0_estimate(*m, p, y0, dt, rtol, atol);
+}
+
+double oracle_h0_m(const OMech* m, double p, const double* y0, double dt, double rtol, double atol, int method) {
+  return h0_estimate(*m, p, y0, dt, rtol, atol, tableau(method).q);
 }
 
 double oracle_enthalpy_mass(const OMech* m, double T, const double* Y) { return enthalpy_mass(*m, T, Y); }
@@ -783,13 +853,14 @@ double oracle_recover_T(const OMech* m, const double* Y, double h_target, double
   return recover_T(*m, Y, h_target, T_guess);
 }
 
-// Integrate n cells over dt. T[n] and Y[n][K] in/out, p[n] in. h0 (nullable):
-// per-cell initial step; <= 0 or NULL selects the starting-step heuristic.
-// Per-cell outputs are nullable. Returns the number of cells with status != 0.
+// Integrate n cells over dt with `method` (0 RODAS4, 1 ROS34PW2; W = the analytic
+// Jacobian). T[n] and Y[n][K] in/out, p[n] in. h0 (nullable): per-cell initial
+// step; <= 0 or NULL selects the starting-step heuristic. Per-cell outputs are
+// nullable. Returns the number of cells with status != 0.
 int64_t oracle_integrate(const OMech* m, int64_t n_cells, double* T, const double* p, double* Y,
                          double dt, double rtol, double atol, int32_t max_steps, const double* h0,
                          int32_t* substeps, int32_t* rejects, double* h_first, int32_t* status,
-                         double* T_ode, int32_t n_threads) {
+                         double* T_ode, int32_t n_threads, int32_t method) {
   const int K = m->K;
   int64_t failed = 0;
 #ifdef _OPENMP
@@ -801,7 +872,7 @@ int64_t oracle_integrate(const OMech* m, int64_t n_cells, double* T, const doubl
     y[0] = T[c];
     for (int k = 0; k < K; ++k) y[1 + k] = Y[(size_t)c * K + k];
     double hi = h0 ? h0[c] : 0.0;
-    CellResult r = integrate_cell(*m, p[c], y.data(), dt, rtol, atol, max_steps, hi);
+    CellResult r = integrate_cell(*m, p[c], y.data(), dt, rtol, atol, max_steps, hi, method);
     T[c] = y[0];
     for (int k = 0; k < K; ++k) Y[(size_t)c * K + k] = y[1 + k];
     if (substeps) substeps[c] = r.substeps;

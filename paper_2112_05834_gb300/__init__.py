@@ -46,6 +46,7 @@ SIGNATURES = {
     "chem_eval_mixture_fraction": (C.c_int, [_P, _I64, _P, _P, _P]),
     "chem_get_reference_mapping": (C.c_int, [_P, _P, _P, _P, _P]),
     "chem_rosenbrock_tableau": (None, [_P, _P, _P, _P, _P]),
+    "chem_method_tableau": (_I32, [_I32, _P, _P, _P, _P, _P]),
     "chem_get_phase_cycles": (C.c_int, [_P, _P, _P, _I32]),
     "chem_mlp_create": (C.c_int, [_I32, C.c_uint64, _P]),
     "chem_mlp_destroy": (C.c_int, [_P]),
@@ -333,6 +334,20 @@ def tableau():
                                    c.ctypes.data_as(C.c_void_p), m.ctypes.data_as(C.c_void_p),
                                    e.ctypes.data_as(C.c_void_p))
     return g.value, a, c, m, e
+
+
+def method_tableau(method):
+    """(gamma, a, c, m, e) of option "method" (0 RODAS4, 1 ROS34PW2) in the device
+    stepper's transformed form, trimmed to the method's stages (host call)."""
+    g = C.c_double()
+    a, c = np.zeros((6, 6)), np.zeros((6, 6))
+    m, e = np.zeros(6), np.zeros(6)
+    s = load().chem_method_tableau(int(method), C.byref(g), a.ctypes.data_as(C.c_void_p),
+                                   c.ctypes.data_as(C.c_void_p), m.ctypes.data_as(C.c_void_p),
+                                   e.ctypes.data_as(C.c_void_p))
+    if s < 0:
+        raise ValueError(f"unknown method {method}")
+    return g.value, a[:s, :s], c[:s, :s], m[:s], e[:s]
 
 
 class CostModel:

@@ -18,6 +18,7 @@
 #include "chem_kernels.h"
 #include "chem_mlp_internal.h"
 #include "rodas4.h"
+#include "ros34pw2.h"
 
 using namespace chem;
 
@@ -35,6 +36,64 @@ static std::string cuda_msg(const char* what, cudaError_t e) {
       return e_ == cudaErrorMemoryAllocation ? CHEM_ERR_OOM : CHEM_ERR_CUDA; \
     }                                                        \
   } while (0)
+
+// ---------------------------------------------------------------------------
+// Rosenbrock methods in the device stepper's transformed form
+// ---------------------------------------------------------------------------
+// RODAS4 is published in that form (rodas4.h). ROS34PW2 is published in the
+// original form (ros34pw2.h) and converted with u_i = sum_j gamma_ij k_j
+// (Hairer & Wanner II, Sec. IV.7): a = alpha Gamma^-1, c = diag(1/gamma) - Gamma^-1,
+// m = b^T Gamma^-1, e = (b - bhat)^T Gamma^-1.
+MethodTab chem::method_tableau(int method) {
+  MethodTab t{};
+  if (method == METHOD_ROS34PW2) {
+    const int S = 4;
+    t.s = S;
+    t.q = 3;
+    t.e_last = 0;
+    t.gamma = kRos34Gamma;
+    double G[4][4] = {}, Gi[4][4] = {};
+    for (int i = 0; i < S; ++i)
+      for (int j = 0; j < S; ++j) G[i][j] = i == j ? kRos34Gamma : kRos34Gam[i][j];
+    // inverse of the lower triangular Gamma, column by column (forward substitution)
+    for (int j = 0; j < S; ++j)
+      for (int i = j; i < S; ++i) {
+        double v = i == j ? 1.0 : 0.0;
+        for (int l = j; l < i; ++l) v -= G[i][l] * Gi[l][j];
+        Gi[i][j] = v / G[i][i];
+      }
+    for (int i = 0; i < S; ++i)
+      for (int j = 0; j < S; ++j) {
+        double a = 0.0;
+        for (int l = 0; l < S; ++l) a += kRos34Alpha[i][l] * Gi[l][j];
+        t.a[i][j] = j < i ? a : 0.0;
+        t.c[i][j] = j < i ? -Gi[i][j] : 0.0;  // the diagonal 1/gamma - Gi_ii is zero
+      }
+    for (int j = 0; j < S; ++j) {
+      double m = 0.0, e = 0.0;
+      for (int l = 0; l < S; ++l) {
+        m += kRos34B[l] * Gi[l][j];
+        e += (kRos34B[l] - kRos34Bhat[l]) * Gi[l][j];
+      }
+      t.m[j] = m;
+      t.e[j] = e;
+    }
+    return t;
+  }
+  t.s = 6;
+  t.q = 4;
+  t.e_last = 1;
+  t.gamma = kRodasGamma;
+  for (int i = 0; i < 6; ++i) {
+    for (int j = 0; j < 6; ++j) {
+      t.a[i][j] = kRodasA[i][j];
+      t.c[i][j] = kRodasC[i][j];
+    }
+    t.m[i] = kRodasM[i];
+    t.e[i] = kRodasE[i];
+  }
+  return t;
+}
 
 // ---------------------------------------------------------------------------
 // mechanism validation
@@ -579,6 +638,7 @@ static const OptionDef kOptions[] = {
     {"jacobian", &chem_handle_s::jac_fd, 0, 1},
     {"pivoting", &chem_handle_s::pivoting, 0, 1},
     {"job_launch", &chem_handle_s::job_launch, 0, 1},
+    {"method", &chem_handle_s::method, 0, 1},
 };
 
 extern "C" chem_status chem_set_option(chem_handle h, const char* key, double value) {
@@ -693,6 +753,7 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
   a.queue = static_cast<int*>(h0->d_queue);
   a.perm = nullptr;
   a.phase = nullptr;
+  a.tab = method_tableau(h0->method);
   if (h0->profile) {
     if (!h0->d_phase) {
       chem_status ps = chem_internal_alloc(h0, &h0->d_phase, 8 * sizeof(unsigned long long));
@@ -1045,7 +1106,8 @@ extern "C" chem_status chem_eval_h0(chem_handle h, int64_t n, const double* T, c
                                     double dt, double rtol, double atol, double* h0, void* stream) {
   if (!h || n < 0 || (n > 0 && (!T || !p || !Y || !h0)) || bad_tol(dt, rtol, atol)) return CHEM_ERR_INVALID_ARG;
   if (n == 0) return CHEM_OK;
-  CHEM_CUDA(h, launch_diag(h->dm, n, T, p, Y, h0, dt, rtol, atol, 2, h->precision, static_cast<cudaStream_t>(stream)));
+  CHEM_CUDA(h, launch_diag(h->dm, n, T, p, Y, h0, dt, rtol, atol, 2, h->precision, static_cast<cudaStream_t>(stream),
+                           0, method_tableau(h->method).q));
   return CHEM_OK;
 }
 
@@ -1075,4 +1137,19 @@ extern "C" void chem_rosenbrock_tableau(double* gamma, double* a, double* c, dou
     if (m) m[i] = kRodasM[i];
     if (e) e[i] = kRodasE[i];
   }
+}
+
+extern "C" int32_t chem_method_tableau(int32_t method, double* gamma, double* a, double* c, double* m, double* e) {
+  if (method < 0 || method > 1) return -1;
+  const MethodTab t = method_tableau(method);
+  if (gamma) *gamma = t.gamma;
+  for (int i = 0; i < 6; ++i) {
+    for (int j = 0; j < 6; ++j) {
+      if (a) a[6 * i + j] = t.a[i][j];
+      if (c) c[6 * i + j] = t.c[i][j];
+    }
+    if (m) m[i] = t.m[i];
+    if (e) e[i] = t.e[i];
+  }
+  return t.s;
 }

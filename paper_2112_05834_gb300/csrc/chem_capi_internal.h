@@ -43,6 +43,7 @@ struct chem_handle_s {
   int jac_fd = 0;                         // option "jacobian": 1 = forward differences (FP64 form)
   int pivoting = 1;                       // option "pivoting": 0 = no row interchanges (FP64 form)
   int job_launch = 0;                     // option "job_launch": 1 = one launch per job, concurrent streams
+  int method = 0;                         // option "method": 0 = RODAS4, 1 = ROS34PW2 (W-method)
   cudaStream_t side = nullptr;            // the handle's stream for concurrent jobs
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t kev0 = nullptr, kev1 = nullptr;

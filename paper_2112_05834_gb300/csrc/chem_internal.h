@@ -22,6 +22,21 @@ constexpr double kTmin = 200.0, kTmax = 6000.0;
 enum Precision { PREC_FP64 = 0, PREC_MIXED = 1, PREC_FP32ASM = 2 };
 enum Sched { SCHED_PLAIN = 0, SCHED_STATIC = 1, SCHED_QUEUE = 2 };
 
+// Rosenbrock methods of the stepper: RODAS4 (order 4, exact Jacobian) or the
+// ROS34PW2 W-method (order 3 for any approximation of the Jacobian).
+enum Method { METHOD_RODAS4 = 0, METHOD_ROS34PW2 = 1 };
+
+// A method in the transformed form of the device stepper, u_i = sum_j gamma_ij k_j:
+//   (I/(h gamma) - W) u_i = f(y0 + sum_{j<i} a_ij u_j) + sum_{j<i} (c_ij / h) u_j,
+//   y1 = y0 + sum m_i u_i, error estimate y1 - yhat = sum e_i u_i.
+struct MethodTab {
+  int s;       // stages (<= 6)
+  int q;       // embedded order + 1: step-size factor err^(-1/q) and starting-step exponent 1/q
+  int e_last;  // 1: the error estimate is the last stage's u (e = unit vector)
+  double gamma;
+  double a[6][6], c[6][6], m[6], e[6];
+};
+
 // Reaction kinds after the host sorts reactions by kind (warp-uniform branches).
 enum RxnKind { RK_ELEM = 0, RK_TB = 1, RK_LIND = 2, RK_TROE = 3 };
 
@@ -106,6 +121,10 @@ struct IntegrateArgs {
   unsigned long long* phase;  // optional [8] per-phase cycle counters (diagnostic)
   double* m0_scratch;  // mixed form, persistent grids: per-CTA slots for the FP64 assembled
   int64_t m0_stride;   //   matrix (null: it stays in shared memory); doubles per slot
+  MethodTab tab;       // the Rosenbrock method
 };
+
+// The transformed tableau of a method (host; chem_capi.cu).
+MethodTab method_tableau(int method);
 
 }  // namespace chem

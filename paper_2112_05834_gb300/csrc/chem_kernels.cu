@@ -322,10 +322,6 @@ __device__ __forceinline__ double xrcp(double x) {
   return fma(r, e, r);
 }
 
-// Rosenbrock coefficients in constant memory (stages are indexed at run time).
-__constant__ double c_rodasA[6][6] = CHEM_RODAS_A;
-__constant__ double c_rodasC[6][6] = CHEM_RODAS_C;
-__constant__ double c_rodasM[6] = CHEM_RODAS_M;
 
 // Precision policy: LU = type of the factorised matrix, ASM = type the Jacobian is
 // assembled in; IR = refine each solve against the assembled matrix.
@@ -1388,10 +1384,11 @@ __device__ void fd_matrix(const DevMech& m, Cta<NW>& c, double p, const double* 
 }
 
 // WRMS norm of e with scale atol + rtol max(|ya|, |yb|). With step_fac, also the
-// step-size factor 0.9 err^(-1/4) (kFacMax for err = 0); both come from the CTA's last warp.
+// step-size factor 0.9 err^(-1/q) (q = 4: RODAS4, 3: ROS34PW2; kFacMax for err = 0);
+// both come from the CTA's last warp.
 template <int NW>
 __device__ double wrms(Cta<NW>& c, int n, const double* e, const double* ya, const double* yb,
-                       double rtol, double atol, double* step_fac = nullptr) {
+                       double rtol, double atol, double* step_fac = nullptr, int q = 4) {
   constexpr int NT = NW * 32;
   double part[1] = {0.0};
   for (int i = c.tid; i < n; i += NT) {
@@ -1403,18 +1400,19 @@ __device__ double wrms(Cta<NW>& c, int n, const double* e, const double* ya, con
   c.reduce(part, warps_for<NW>(n), [&](const double (&t)[1], double (&r)[2]) {
     const double err = sqrt(t[0] / n);
     r[0] = err;
-    r[1] = err > 0.0 ? kSafety / sqrt(sqrt(err)) : kFacMax;
+    r[1] = err > 0.0 ? kSafety / (q == 4 ? sqrt(sqrt(err)) : cbrt(err)) : kFacMax;
   }, o);
   if (step_fac) *step_fac = o[1];
   return o[0];
 }
 
 // Hairer-Wanner starting step (Solving ODEs I, Sec. II.4) in the WRMS norm with
-// scale atol + rtol |y0|, exponent 1/4, clamped to dt; a vanishing derivative
-// selects the whole interval. Uses f0 = f(y0) (already in c.f0) and c.ys, c.fv.
+// scale atol + rtol |y0|, exponent 1/q (the method's embedded order + 1), clamped
+// to dt; a vanishing derivative selects the whole interval. Uses f0 = f(y0)
+// (already in c.f0) and c.ys, c.fv.
 template <int NW, bool FF = false>
 __device__ double starting_step(const DevMech& m, Cta<NW>& c, double p, double dt, double rtol,
-                                double atol) {
+                                double atol, int q = 4) {
   constexpr int NT = NW * 32;
   const int n = m.K + 1;
   const double d0 = wrms(c, n, c.y, c.y, c.y, rtol, atol);
@@ -1428,7 +1426,7 @@ __device__ double starting_step(const DevMech& m, Cta<NW>& c, double p, double d
   __syncthreads();
   const double d2 = wrms(c, n, c.rr, c.y, c.y, rtol, atol) / ha;
   const double mx = fmax(d1, d2);
-  const double hb = (mx > 1e-300) ? pow(0.01 / mx, 0.25) : dt;
+  const double hb = (mx > 1e-300) ? (q == 4 ? pow(0.01 / mx, 0.25) : cbrt(0.01 / mx)) : dt;
   return fmin(fmin(100.0 * ha, hb), dt);
 }
 
@@ -1507,7 +1505,7 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
     }
     if (h <= 0.0) {
       eval_rhs<NW, false, Policy<PREC>::IR>(m, c, c.y, p, c.f0);
-      h = starting_step<NW, Policy<PREC>::IR>(m, c, p, dt, rtol, atol);
+      h = starting_step<NW, Policy<PREC>::IR>(m, c, p, dt, rtol, atol, args.tab.q);
     }
     double t = 0.0, h_unclipped = h;
     bool after_reject = false;
@@ -1538,12 +1536,12 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
         eval_rhs<NW, false, false>(m, c, c.y, p, c.f0);
         apply_guard();
         PHASE(2);
-        fd_matrix<NW, false>(m, c, p, c.y, c.f0, 1.0 / (h * kRodasGamma));
+        fd_matrix<NW, false>(m, c, p, c.y, c.f0, 1.0 / (h * args.tab.gamma));
       } else {
         const Scal s = eval_rhs<NW, true, Policy<PREC>::IR>(m, c, c.y, p, c.f0);
         apply_guard();
         PHASE(2);
-        build_matrix<NW, PREC, false>(m, c, s, c.f0, 1.0 / (h * kRodasGamma));
+        build_matrix<NW, PREC, false>(m, c, s, c.f0, 1.0 / (h * args.tab.gamma));
       }
       PHASE(3);
       const int info = factor<NW, PREC>(c, n, !(PREC == PREC_FP64 && args.no_pivot));
@@ -1553,14 +1551,16 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
         err = NAN;
       } else {
         const double invh = 1.0 / h;
+        const MethodTab& tb = args.tab;
+        const int S = tb.s;
 #pragma unroll 1
-        for (int st = 0; st < 6; ++st) {
+        for (int st = 0; st < S; ++st) {
           const double* fs = c.f0;
           if (st > 0) {
             PHASE(6);
             for (int i = c.tid; i < n; i += NT) {
               double v = c.y[i];
-              for (int j = 0; j < st; ++j) v += c_rodasA[st][j] * c.u[j * n + i];
+              for (int j = 0; j < st; ++j) v += tb.a[st][j] * c.u[j * n + i];
               c.ys[i] = v;
             }
             __syncthreads();
@@ -1572,7 +1572,7 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
           // stage right-hand side f(y_s) + sum_j (c_sj / h) u_j, in place in fv
           for (int i = c.tid; i < n; i += NT) {
             double v = 0.0;
-            for (int j = 0; j < st; ++j) v += c_rodasC[st][j] * c.u[j * n + i];
+            for (int j = 0; j < st; ++j) v += tb.c[st][j] * c.u[j * n + i];
             c.fv[i] = fma(invh, v, fs[i]);
           }
           __syncthreads();
@@ -1581,13 +1581,16 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
         }
         PHASE(6);
         for (int i = c.tid; i < n; i += NT) {
-          double v = c.y[i];
-#pragma unroll
-          for (int j = 0; j < 6; ++j) v += c_rodasM[j] * c.u[j * n + i];
+          double v = c.y[i], e = 0.0;
+          for (int j = 0; j < S; ++j) {
+            v += tb.m[j] * c.u[j * n + i];
+            if (!tb.e_last) e += tb.e[j] * c.u[j * n + i];
+          }
           c.yn[i] = v;
+          if (!tb.e_last) c.rr[i] = e;
         }
         __syncthreads();
-        err = wrms(c, n, c.u + 5 * n, c.y, c.yn, rtol, atol, &step_fac);
+        err = wrms(c, n, tb.e_last ? c.u + (S - 1) * n : c.rr, c.y, c.yn, rtol, atol, &step_fac, tb.q);
       }
       if (!(err <= 1.0)) {
         ++rejects;
@@ -1686,6 +1689,7 @@ struct DiagArgs {
   double dt, rtol, atol;
   int what;    // 0 rhs, 1 jacobian, 2 h0
   int jac_fd;  // FP64 form: forward-difference Jacobian for what = 1
+  int q;       // starting-step exponent 1/q (the method's embedded order + 1)
 };
 
 template <int NW, int PREC>
@@ -1719,7 +1723,7 @@ __global__ void __launch_bounds__(NW * 32) k_diag(const __grid_constant__ DiagAr
         for (int j = c.lane; j < n; j += 32) a.out[(size_t)cell * n * n + i * n + j] = (double)J[i * ld + j];
     } else {
       eval_rhs<NW, false, Policy<PREC>::IR>(a.m, c, c.y, p, c.f0);
-      const double h = starting_step<NW, Policy<PREC>::IR>(a.m, c, p, a.dt, a.rtol, a.atol);
+      const double h = starting_step<NW, Policy<PREC>::IR>(a.m, c, p, a.dt, a.rtol, a.atol, a.q);
       if (c.tid == 0) a.out[cell] = h;
     }
     __syncthreads();
@@ -1833,9 +1837,10 @@ static cudaError_t launch_simple(KernelT k, const ArgT& a, size_t smem, int grid
 
 cudaError_t launch_diag(const DevMech& m, int64_t n, const double* T, const double* p, const double* Y,
                         double* out, double dt, double rtol, double atol, int what, int prec,
-                        cudaStream_t st, int jac_fd) {
+                        cudaStream_t st, int jac_fd, int q) {
   DiagArgs a;
   a.jac_fd = jac_fd;
+  a.q = q;
   a.m = m;
   a.n = n;
   a.T = T;

@@ -127,6 +127,7 @@ extern "C" chem_status chem_integrate_noalloc(chem_handle h, int64_t n_cells, do
   a.jac_fd = h->jac_fd;
   a.no_pivot = h->pivoting ? 0 : 1;
   a.use_h0 = 0;
+  a.tab = chem::method_tableau(h->method);
   a.smem_K = h->K;
   a.smem_I = h->I > 0 ? h->I : 1;
   const int block = h->block ? h->block : chem_internal_pick_block(h, a.smem_K, a.smem_I);

@@ -64,6 +64,26 @@ def test_tableau_order_conditions(lib):
     assert np.abs(_order_conditions(alpha, G, bhat)[:4]).max() < 1e-13
 
 
+def test_w_method_tableau(lib):
+    """The device tableau of option method = 1 (transformed form, converted on the host
+    from the published coefficients) maps back to a W-method of order 3 with an
+    embedded W-order 2, written independently of the oracle's table."""
+    import paper_2112_05834_gb300 as pkg
+    from test_oracle_pins import _w_order_conditions
+
+    g, a, c, m, e = pkg.method_tableau(1)
+    assert a.shape == (4, 4)
+    G = np.linalg.inv(np.eye(4) / g - c)
+    alpha = np.tril(a @ G, -1)
+    res = _w_order_conditions(alpha, G, m @ G)
+    assert np.abs(res).max() < 1e-13, res
+    assert np.abs(_w_order_conditions(alpha, G, (m - e) @ G)[:3]).max() < 1e-13
+    g0, a0, c0, m0, e0 = pkg.method_tableau(0)
+    assert a0.shape == (6, 6) and g0 == 0.25 and np.all(e0 == [0, 0, 0, 0, 0, 1])
+    with pytest.raises(ValueError):
+        pkg.method_tableau(2)
+
+
 def _desc(mech):
     import paper_2112_05834_gb300 as pkg
 

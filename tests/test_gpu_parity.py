@@ -329,6 +329,52 @@ def test_integrate_parity(pkg, orc, name, n, precision):
         assert abs(ratio - 1.0) <= 0.05, ratio
 
 
+_W_REF = {}
+
+
+def _oracle_w_ref(orc, name, n, seed=1):
+    key = (name, n, seed)
+    if key not in _W_REF:
+        m, st, dt = synth.workload(name, n_cells=n, state_seed=seed)
+        _W_REF[key] = orc.integrate(m, st.T, st.p, st.Y, dt, RTOL, ATOL, method="ros34pw2")
+    return _W_REF[key]
+
+
+@pytest.mark.parametrize("name,n", [("h2_10_1k", 1000), ("c54_65k", 333), ("c100_262k", 161)])
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_w_method_parity(pkg, orc, name, n, precision):
+    """Option method = 1 (ROS34PW2 W-method) against the oracle's ROS34PW2 and its
+    RODAS4, at the parity bound, for the FP64, mixed and FP32-assembly forms. With
+    precision 0 and 1 (the same method up to rounding) the step totals agree with the
+    oracle's; with precision 2 the FP32-assembled matrix is a W, and because the
+    method's order does not rely on W being the exact Jacobian its step total stays
+    within 5 % as well (RODAS4 in that form takes about 2.6 times as many)."""
+    m, st, dt, ref4 = _oracle_ref(orc, name, n)
+    refw = _oracle_w_ref(orc, name, n)
+    assert np.all(refw["status"] == 0)
+    g = _run(pkg, m, st, dt, precision=precision, method=1)
+    assert np.all(g["status"] == 0)
+    _assert_bound(g["T"], g["Y"], refw, f"{name} W-method precision={precision} vs oracle ROS34PW2")
+    _assert_bound(g["T"], g["Y"], ref4, f"{name} W-method precision={precision} vs oracle RODAS4")
+    ratio = g["substeps"].sum() / refw["substeps"].sum()
+    print(f"{name} W-method precision={precision}: substeps gpu/oracle = {ratio:.4f} "
+          f"(oracle RODAS4 / ROS34PW2 = {ref4['substeps'].sum() / refw['substeps'].sum():.3f}), "
+          f"rejects gpu {g['rejects'].sum()} oracle {refw['rejects'].sum()}")
+    assert abs(ratio - 1.0) <= 0.05, ratio
+
+
+def test_w_method_starting_step(pkg, orc):
+    """The starting step of method = 1 uses the exponent 1/3 (its embedded order + 1)."""
+    m = synth.mechanism_preset("c_54")
+    st = _states(m, n=16)
+    integ = pkg.Integrator(m, method=1)
+    h = integ.eval_h0(_dev(st.T), _dev(st.p), _dev(st.Y), 1e-6, RTOL, ATOL).cpu().numpy()
+    M = orc.Mech(m)
+    for c in range(16):
+        y = np.concatenate([[st.T[c]], st.Y[c]])
+        np.testing.assert_allclose(h[c], orc.h0(M, st.p[c], y, 1e-6, RTOL, ATOL, method="ros34pw2"), rtol=1e-10)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_conservation_on_gpu(pkg, orc, precision):
     m, st, dt, ref = _oracle_ref(orc, "c54_65k", 333)

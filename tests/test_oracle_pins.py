@@ -84,6 +84,76 @@ def test_rodas4_empirical_local_order(oracle_lib):
     assert 3.6 < se < 4.4, (se, ee)
 
 
+def _w_order_conditions(alpha, gam, b):
+    """Residuals of the order conditions up to order 3 of a W-method (W any matrix in
+    place of the Jacobian). Expanding the stages k_i = h f(y0 + sum alpha_ij k_j) +
+    h W sum_{j<=i} gamma_ij k_j in powers of h, with a_i = sum_j alpha_ij and
+    g_i = sum_{j<=i} gamma_ij: order h^2 carries f'f (weight b.a) and W f (b.g), order
+    h^3 carries f''(f,f) (b.a^2 / 2), f'f'f (b A a), f'W f (b A g), W f'f (b G a) and
+    W W f (b G g). Every term containing W must vanish and the others must match the
+    exact solution's Taylor series (1, 1/2, 1/6 (f''(f,f) + f'f'f))."""
+    A = np.tril(alpha, -1)
+    a = A.sum(axis=1)
+    g = gam.sum(axis=1)
+    return np.array([b.sum() - 1.0, b @ a - 0.5, b @ g,
+                     b @ a ** 2 - 1.0 / 3.0, b @ (A @ a) - 1.0 / 6.0, b @ (A @ g), b @ (gam @ a), b @ (gam @ g)])
+
+
+def test_ros34pw2_order_conditions(oracle_lib):
+    """ROS34PW2 (Rang & Angermann 2005): W-order 3 for the main solution and W-order 2
+    (and not 3) for the embedded one; hence also Rosenbrock order 3 with the exact
+    Jacobian; stiffly accurate (b = last row of alpha + Gamma); L-stable, with gamma the
+    root of 6 g^3 - 18 g^2 + 9 g - 1 near 0.4359 (R(z) -> 0 as z -> -inf)."""
+    alpha, gam, b, bhat, q = oracle_lib.tableau_of("ros34pw2")
+    assert alpha.shape == (4, 4) and q == 3.0
+    main = _w_order_conditions(alpha, gam, b)
+    emb = _w_order_conditions(alpha, gam, bhat)
+    assert np.abs(main).max() < 1e-14, main
+    assert np.abs(emb[:3]).max() < 1e-14, emb
+    assert np.abs(emb[3:]).max() > 1e-3
+    assert np.abs(_order_conditions(alpha, gam, b)[:4]).max() < 1e-14
+    g = gam[0, 0]
+    np.testing.assert_allclose(np.diag(gam), g, rtol=0, atol=0)
+    assert abs(6 * g ** 3 - 18 * g ** 2 + 9 * g - 1) < 1e-14 and abs(g - 0.4358665215) < 1e-10
+    beta = alpha + gam
+    np.testing.assert_allclose(b, beta[3], atol=1e-15)
+    # stability function at -infinity: R = 1 - b^T (alpha + Gamma)^-1 1
+    r_inf = 1.0 - b @ np.linalg.solve(beta, np.ones(4))
+    assert abs(r_inf) < 1e-13
+    # RODAS4 is not a W-method: already the order-2 W condition b.g = 0 fails
+    a4, g4, b4, _, _ = oracle_lib.tableau_of("rodas4")
+    assert abs(_w_order_conditions(a4, g4, b4)[2]) > 1e-2
+
+
+def test_w_method_keeps_its_order_with_a_wrong_jacobian(oracle_lib):
+    """Local error of one step with W = J + E, E a fixed random matrix of 30 % of |J|'s
+    largest entry, against 256 RODAS4 substeps with the exact Jacobian, on the smooth
+    dimerisation problem: ROS34PW2 keeps slopes ~4 (order 3) and ~3 (embedded order 2),
+    RODAS4 falls to ~2 (order 1)."""
+    M = oracle_lib.Mech(mechs.dimerization())
+    y0 = np.array([1000.0, 0.6, 0.4, 0.0])
+    p = 1e6
+    J = oracle_lib.jac(M, p, y0)
+    E = np.random.default_rng(0).standard_normal(J.shape) * 0.3 * np.abs(J).max()
+    hs = [2e-5 * 2.0 ** -k for k in range(1, 6)]
+
+    def slopes(method):
+        em, ee = [], []
+        for h in hs:
+            y1, yh = oracle_lib.row_step(M, p, y0, h, method, E)
+            y = y0.copy()
+            for _ in range(256):
+                y, _ = oracle_lib.row_step(M, p, y, h / 256, "rodas4")
+            em.append(np.abs(y1 - y)[1:].max())
+            ee.append(np.abs(yh - y)[1:].max())
+        return np.polyfit(np.log(hs), np.log(em), 1)[0], np.polyfit(np.log(hs), np.log(ee), 1)[0]
+
+    sm, se = slopes("ros34pw2")
+    assert abs(sm - 4.0) < 0.3 and abs(se - 3.0) < 0.3, (sm, se)
+    sm4, _ = slopes("rodas4")
+    assert abs(sm4 - 2.0) < 0.3, sm4
+
+
 # ------------------------------------------------------------------ thermo / rates
 def test_thermo_identities(oracle_lib):
     """d(H/R)/dT = cp/R, d(S/R)/dT = cp/(R T) (central differences), including across
