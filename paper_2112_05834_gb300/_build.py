@@ -44,7 +44,7 @@ def _stale(target, deps):
 def build(verbose: bool = False, force: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nv = _nvcc()
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(ROOT, "include", "chem.h"))
     srcs = sources()
     objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]

@@ -1,1685 +1,17 @@
-// Device code of the batched stiff-chemistry integrator (sm_103a).
-//
-// One CTA integrates one cell at a time; its warps share the cell's work:
-// species and 32-reaction chunks are dealt over threads and warps for the rates,
-// Jacobian rows over warps (columns over lanes) for the assembly; the FP64 form
-// factorises in shared memory (rows over warps) and solves on one warp, the mixed
-// form inverts in FP32 with the matrix in registers (columns over warps, rows over
-// lanes) and solves by matrix-vector products over all threads. All per-cell data
-// (state, stage vectors, per-reaction derivative data, the iteration matrix) lives
-// in shared memory, except that the mixed form may keep its FP64 assembled matrix
-// in a global-memory slot of the CTA when that lets more CTAs share an SM; the
-// mechanism tables are read through the L1 cache.
-//
-// Paper mapping: rates and RHS = pyJac's reaction-rate evaluation; analytic
-// Jacobian = pyJac's Jacobian (Methodology, "Analytical Jacobian and improved ODE
-// solution"); LU + substitution = the LAPACK replacement of OpenFOAM's linear
-// algebra (same section); the per-cell loop = the implicit ODE solver of the
-// Introduction; the work queue = DLBFoam's redistribution of cell problems
-// (Methodology, "DLBFoam: Dynamic load balancing"), reinterpreted inside one GPU.
+// Diagnostic kernels and host launchers of the batched stiff-chemistry integrator
+// (sm_103a); the device code shared with chem_kernels_w.cu is in chem_device.cuh.
+// This translation unit instantiates the integration kernel with the RODAS4 stepper.
 
-#include <cuda_runtime.h>
-
-#include <cfloat>
-#include <cmath>
-#include <cstdint>
-#include <type_traits>
-
-#include "chem.h"
-#include "chem_internal.h"
-#include "chem_kernels.h"
-#include "rodas4.h"
+#include "chem_device.cuh"
 
 namespace chem {
-
-#define FULLMASK 0xffffffffu
-
-// ---------------------------------------------------------------------------
-// Float-float arithmetic (a value is hi + lo with two FP32 numbers): error-free
-// products with FMA (Dekker/Ogita-Rump-Oishi style TwoProduct) and TwoSum
-// (Knuth) give about 44-48 significant bits on the FP32 pipe, which on GB300
-// runs ~60x faster than the FP64 pipe. Used by the mixed form for long sums of
-// products (third-body concentrations, refinement residuals).
-// ---------------------------------------------------------------------------
-struct ff2 {
-  float hi, lo;
-};
-__device__ __forceinline__ ff2 ff_split(double x) {
-  const float h = (float)x;
-  return {h, (float)(x - (double)h)};
-}
-__device__ __forceinline__ double ff_value(ff2 a) { return (double)a.hi + (double)a.lo; }
-// s + p (both float-float), renormalised
-__device__ __forceinline__ ff2 ff_add(ff2 a, ff2 b) {
-  const float s = a.hi + b.hi;
-  const float bb = s - a.hi;
-  float e = (a.hi - (s - bb)) + (b.hi - bb);
-  e += a.lo + b.lo;
-  const float h = s + e;
-  return {h, e - (h - s)};
-}
-// a * b (both float-float); the lo * lo term is below the precision kept
-__device__ __forceinline__ ff2 ff_mul(ff2 a, ff2 b) {
-  const float p = a.hi * b.hi;
-  float e = fmaf(a.hi, b.hi, -p);
-  e = fmaf(a.hi, b.lo, e);
-  e = fmaf(a.lo, b.hi, e);
-  const float h = p + e;
-  return {h, e - (h - p)};
-}
-
-// ---------------------------------------------------------------------------
-// Exponential by Tang's table-driven method (P. T. P. Tang, "Table-driven
-// implementation of the exponential function in IEEE floating-point arithmetic",
-// ACM TOMS 15(2), 1989): x = (32 m + j) ln2/32 + r with |r| <= ln2/64, so
-// exp(x) = 2^m 2^(j/32) exp(r). 2^(j/32) comes from a table of (lead, trail) pairs
-// (lead = 2^(j/32) rounded to double, trail = the remainder rounded to double),
-// exp(r) - 1 from its Taylor polynomial of degree 6 (truncation below 4e-18
-// relative), ln2/32 as a two-term split for the reduction, and 2^m is added to the
-// exponent field. |x| >= 672, infinities and NaN take the library exp. About 11
-// FP64 instructions against ~16 for the library routine on this part.
-// ---------------------------------------------------------------------------
-__device__ const double2 g_exp2_tab[32] = {
-    {1.0, 0.0},
-    {1.0218971486541166, 5.109225028973444e-17},
-    {1.0442737824274138, 8.551889705537965e-17},
-    {1.0671404006768237, -7.899853966841582e-17},
-    {1.0905077326652577, -3.046782079812471e-17},
-    {1.1143867425958924, 1.0410278456845571e-16},
-    {1.1387886347566916, 8.912812676025408e-17},
-    {1.1637248587775775, 3.8292048369240935e-17},
-    {1.189207115002721, 3.982015231465646e-17},
-    {1.215247359980469, -7.712630692681488e-17},
-    {1.241857812073484, 4.658027591836937e-17},
-    {1.2690509571917332, 2.667932131342186e-18},
-    {1.2968395546510096, 2.5382502794888315e-17},
-    {1.3252366431597413, -2.8587312100388614e-17},
-    {1.3542555469368927, 7.70094837980299e-17},
-    {1.383909881963832, -6.770511658794786e-17},
-    {1.4142135623730951, -9.667293313452913e-17},
-    {1.4451808069770467, -3.0237581349939873e-17},
-    {1.4768261459394993, -3.483994556892796e-17},
-    {1.5091644275934228, -1.016455327754295e-16},
-    {1.5422108254079407, 7.949834809697621e-17},
-    {1.5759808451078865, -1.0136916471278304e-17},
-    {1.6104903319492543, 2.4707192569797888e-17},
-    {1.645755478153965, -1.0125679913674773e-16},
-    {1.681792830507429, 8.199010020581497e-17},
-    {1.718619298122478, -1.851380418263111e-17},
-    {1.7562521603732995, 2.960140695448873e-17},
-    {1.7947090750031072, 1.8227458427912087e-17},
-    {1.8340080864093424, 3.283107224245627e-17},
-    {1.8741676341103, -6.122763413004143e-17},
-    {1.9152065613971474, -1.0619946056195963e-16},
-    {1.9571441241754002, 8.960767791036668e-17}
-};
-
-__device__ __noinline__ double exp_outside(double x) { return exp(x); }
-
-constexpr double kInvLn10 = 0.43429448190325176;  // 1 / ln 10
-// Largest |G/RT| of a species for which the reverse-rate ratio is formed as a
-// product of per-species factors exp(+-G/RT): four factors stay within e^+-600.
-constexpr double kBigGRT = 150.0;
-constexpr double kLnRcP0 = 4.407418589020958;  // ln(Rc / P0), cgs
-
-__device__ __forceinline__ double xexp(double x, const double2* tab) {
-  if ((__double2hiint(x) & 0x7fffffff) >= 0x40850000) return exp_outside(x);  // |x| >= 672, inf, NaN
-  constexpr double kInvL = 46.16624130844683;      // 32 / ln 2
-  constexpr double kL1 = 0.02166084939249829;      // ln2/32 rounded to double
-  constexpr double kL2 = 7.247021293269686e-19;    // ln2/32 - kL1
-  constexpr double kShift = 6755399441055744.0;    // 1.5 * 2^52: rounds to an integer in the low word
-  const double t = fma(x, kInvL, kShift);
-  const int N = __double2loint(t);
-  const double Nd = t - kShift;
-  double r = fma(-Nd, kL1, x);
-  r = fma(-Nd, kL2, r);
-  double q = fma(r, 1.0 / 720.0, 1.0 / 120.0);
-  q = fma(r, q, 1.0 / 24.0);
-  q = fma(r, q, 1.0 / 6.0);
-  q = fma(r, q, 0.5);
-  const double em1 = fma(r * r, q, r);  // exp(r) - 1
-  const double2 sj = tab[N & 31];
-  const double y = sj.x + fma(sj.x, em1, sj.y);
-  return __hiloint2double(__double2hiint(y) + (N >> 5) * (1 << 20), __double2loint(y));
-}
-
-// ---------------------------------------------------------------------------
-// Natural logarithm, table-driven in the manner of Tang (P. T. P. Tang, "Table-
-// driven implementation of the logarithm function in IEEE floating-point
-// arithmetic", ACM TOMS 16(4), 1990): x = 2^m y with y in [1, 2), F = 1 + j/128 the
-// nearest of 129 points, c = 1/F rounded to double, r = y c - 1 (one FMA rounding,
-// |r| <= 1/256 + 2^-30), and ln x = m ln 2 - ln c + ln(1 + r), with ln(1 + r) from
-// its Taylor series to degree 7 (truncation below 2e-18 relative). The table holds
-// (c, -ln c as lead + trail) for the rounded c; ln 2 is split so m ln2_hi is exact.
-// Zero, negative, subnormal, infinite and NaN arguments take the library log.
-// ---------------------------------------------------------------------------
-__device__ const double g_log_tab[129][3] = {
-    {1.0, 0.0, 0.0},
-    {0.9922480620155039, 0.007782140442054963, -1.2819179123343749e-20},
-    {0.9846153846153847, 0.015504186535965199, -3.2783210228924137e-19},
-    {0.9770992366412213, 0.023167059281534418, -3.095927552179262e-19},
-    {0.9696969696969697, 0.03077165866675366, 1.0431732029005972e-18},
-    {0.9624060150375939, 0.03831886430213666, -2.3579961573512846e-18},
-    {0.9552238805970149, 0.04580953603129422, 1.6823639049745016e-19},
-    {0.9481481481481482, 0.05324451451881224, 1.803871134979952e-18},
-    {0.9411764705882353, 0.060624621816434854, 2.6424025938726934e-18},
-    {0.9343065693430657, 0.06795066190850778, 3.9239563038692484e-18},
-    {0.927536231884058, 0.07522342123758752, -4.195880720316434e-18},
-    {0.920863309352518, 0.08244366921107454, -4.707903082046854e-18},
-    {0.9142857142857143, 0.08961215868968717, -1.9573659817110993e-18},
-    {0.9078014184397163, 0.09672962645855114, -4.0291867005826106e-18},
-    {0.9014084507042254, 0.10379679368164355, -3.195893222617445e-18},
-    {0.8951048951048951, 0.11081436634029011, 2.0511100808140527e-18},
-    {0.8888888888888888, 0.11778303565638351, -1.1971685747593662e-18},
-    {0.8827586206896552, 0.12470347850095725, -4.6522609636496624e-18},
-    {0.8767123287671232, 0.13157635778871932, 1.112300087972959e-17},
-    {0.8707482993197279, 0.1384023228591192, -1.3766819196398948e-17},
-    {0.8648648648648649, 0.14518200984449783, 8.242418783022477e-18},
-    {0.8590604026845637, 0.151916042025842, 4.1233095848339465e-19},
-    {0.8533333333333334, 0.15860503017663852, 2.583386492298558e-18},
-    {0.847682119205298, 0.16524957289530717, -9.227573884334224e-18},
-    {0.8421052631578947, 0.17185025692665928, -6.022453821011369e-18},
-    {0.8366013071895425, 0.17840765747281825, 1.2720936612962572e-17},
-    {0.8311688311688312, 0.18492233849401193, -7.384679440503435e-18},
-    {0.8258064516129032, 0.19139485299962947, -1.126213516780448e-17},
-    {0.8205128205128205, 0.19782574332991992, -7.995487338741543e-18},
-    {0.8152866242038217, 0.20421554142869083, 7.9379985298027e-18},
-    {0.810126582278481, 0.21056476910734964, 1.136310596906137e-17},
-    {0.8050314465408805, 0.2168739383006143, 6.285749669211092e-18},
-    {0.8, 0.2231435513142097, -9.091270597324798e-18},
-    {0.7950310559006211, 0.2293741010648459, -5.684839459813236e-18},
-    {0.7901234567901234, 0.23556607131276697, -2.394337149518734e-18},
-    {0.7852760736196319, 0.24171993688714513, 1.323779871210866e-17},
-    {0.7804878048780488, 0.2478361639045812, 8.384472133019162e-18},
-    {0.7757575757575758, 0.25391520998096345, -7.180735656435798e-18},
-    {0.7710843373493976, 0.259957524436926, 2.4167516341742964e-17},
-    {0.7664670658682635, 0.2659635484971379, 1.35209848201012e-19},
-    {0.7619047619047619, 0.2719337154836418, 7.833196376974436e-19},
-    {0.757396449704142, 0.2778684510034563, 2.2502748630777633e-17},
-    {0.7529411764705882, 0.2837681731306446, -6.448868003452105e-18},
-    {0.7485380116959064, 0.2896332925830427, 2.0535953219858177e-17},
-    {0.7441860465116279, 0.2954642128938359, -7.768320796245443e-18},
-    {0.7398843930635838, 0.30126133057816185, -1.5120043309967385e-17},
-    {0.735632183908046, 0.3070250352949119, 1.5578716077124932e-18},
-    {0.7314285714285714, 0.3127557100038969, -1.3650721793001109e-17},
-    {0.7272727272727273, 0.3184537311185346, -6.407962483026777e-19},
-    {0.7231638418079096, 0.324119468654212, -4.488767429940198e-18},
-    {0.7191011235955056, 0.32975328637246804, -2.5633554999431966e-17},
-    {0.7150837988826816, 0.3353555419211378, -1.3746739934976202e-17},
-    {0.7111111111111111, 0.3409265869705932, -2.069678002794501e-17},
-    {0.7071823204419889, 0.3464667673462086, -3.591951952851805e-18},
-    {0.7032967032967034, 0.3519764231571781, 2.0005853013367377e-17},
-    {0.6994535519125683, 0.3574558889218038, -2.4269548334425144e-17},
-    {0.6956521739130435, 0.3629054936893685, 6.2632141603179415e-18},
-    {0.6918918918918919, 0.36832556115870757, 2.690672380132659e-17},
-    {0.6881720430107527, 0.373716409793584, -2.449917382477111e-18},
-    {0.6844919786096256, 0.3790783529349695, 1.8481479367349684e-17},
-    {0.6808510638297872, 0.38441169891033206, 8.164631656028572e-18},
-    {0.6772486772486772, 0.38971675114002524, 2.734172667856699e-17},
-    {0.6736842105263158, 0.394993808240869, 7.437680769362324e-18},
-    {0.6701570680628273, 0.40024316412701266, -1.655340963311913e-17},
-    {0.6666666666666666, 0.40546510810816444, -2.881138025962641e-18},
-    {0.6632124352331606, 0.4106599249852683, 2.7752739097728695e-17},
-    {0.6597938144329897, 0.415827895143711, -5.793440801214822e-18},
-    {0.6564102564102564, 0.42096929464412963, 4.5972855136437464e-18},
-    {0.6530612244897959, 0.42608439531090014, -7.056391017993593e-19},
-    {0.649746192893401, 0.43117346481837143, -1.3539234990021841e-17},
-    {0.6464646464646465, 0.43623676677491796, 2.4182887316590065e-17},
-    {0.6432160804020101, 0.4412745608048752, 1.0343758877897315e-17},
-    {0.64, 0.4462871026284195, 1.6511928324886544e-17},
-    {0.6368159203980099, 0.4512746441394586, -9.65179553937242e-18},
-    {0.6336633663366337, 0.4562374334815876, 9.07916350878553e-18},
-    {0.6305418719211823, 0.46117571512217015, 6.140445034134513e-18},
-    {0.6274509803921569, 0.46608972992459924, -2.387354320899491e-19},
-    {0.624390243902439, 0.470979715218791, 7.099457177589995e-18},
-    {0.6213592233009708, 0.475845904869964, 2.5043069845040313e-17},
-    {0.6183574879227053, 0.48068852934575196, -2.7402100563370574e-18},
-    {0.6153846153846154, 0.48550781578170077, -1.6618350693852045e-17},
-    {0.6124401913875598, 0.4903039880451939, 4.612452524535198e-18},
-    {0.6095238095238096, 0.4950772667978514, 1.2508730752094332e-17},
-    {0.6066350710900474, 0.49982786955644926, -2.25665388836583e-18},
-    {0.6037735849056604, 0.5045560107523953, 1.3275397597891851e-17},
-    {0.6009389671361502, 0.5092619017898079, 2.1678544367048826e-17},
-    {0.5981308411214953, 0.5139457511022344, -2.4537074021915265e-18},
-    {0.5953488372093023, 0.5186077642080457, -1.6859591393570242e-17},
-    {0.5925925925925926, 0.5232481437645479, 2.3677269014906905e-17},
-    {0.5898617511520737, 0.5278670896208424, -3.071514383985515e-18},
-    {0.5871559633027523, 0.5324647988694717, 5.4596227307139745e-17},
-    {0.5844748858447488, 0.5370414658968837, -1.9513712761861967e-17},
-    {0.5818181818181818, 0.5415972824327444, 1.108461486609421e-17},
-    {0.579185520361991, 0.5461324375981356, -6.169692458083718e-18},
-    {0.5765765765765766, 0.5506471179526623, -1.3720677478685045e-17},
-    {0.5739910313901345, 0.5551415075405016, -1.449278054403172e-17},
-    {0.5714285714285714, 0.5596157879354228, -2.8656225429134744e-17},
-    {0.5688888888888889, 0.564070138284803, -4.6267923647049475e-17},
-    {0.5663716814159292, 0.5685047353526688, -4.0389558221668317e-17},
-    {0.5638766519823789, 0.5729197535617854, 4.4242614369063874e-17},
-    {0.5614035087719298, 0.5773153650348236, 4.660755938428382e-17},
-    {0.5589519650655022, 0.5816917396346225, 2.7912851075301e-17},
-    {0.5565217391304348, 0.5860490450035782, -4.272669638447342e-17},
-    {0.5541125541125541, 0.5903874466021763, 2.876546074301208e-17},
-    {0.5517241379310345, 0.5947071077466928, 2.7629477772138132e-17},
-    {0.5493562231759657, 0.5990081896460834, 2.5162534548420983e-17},
-    {0.5470085470085471, 0.6032908514380841, 2.0348397202878346e-17},
-    {0.5446808510638298, 0.6075552502245418, -4.1692640626751196e-17},
-    {0.5423728813559322, 0.6118015411059929, -3.392831249677239e-17},
-    {0.540084388185654, 0.616029877215514, 4.9247969628553695e-17},
-    {0.5378151260504201, 0.6202404097518576, 3.4764762563436685e-18},
-    {0.5355648535564853, 0.6244332880118936, 1.4444646832738594e-17},
-    {0.5333333333333333, 0.6286086594223742, -5.360577204673081e-17},
-    {0.5311203319502075, 0.6327666695710378, 5.223564575344447e-17},
-    {0.5289256198347108, 0.6369074622370692, 2.6473983119023558e-17},
-    {0.5267489711934157, 0.6410311794209312, -3.4765774267087093e-17},
-    {0.5245901639344263, 0.6451379613735847, -5.110700818729212e-17},
-    {0.5224489795918368, 0.6492279466251097, -1.3266356651077771e-17},
-    {0.5203252032520326, 0.6533012720127456, -3.7864752792363655e-17},
-    {0.5182186234817814, 0.65735807270836, 2.2462005860533567e-17},
-    {0.5161290322580645, 0.661398482245365, 2.015224182999491e-17},
-    {0.5140562248995983, 0.6654226325450905, 5.424612435933966e-17},
-    {0.512, 0.6694306539426292, 7.420657727561746e-18},
-    {0.5099601593625498, 0.6734226752121667, 3.84128539325942e-17},
-    {0.5079365079365079, 0.6773988235918061, 5.341333284299263e-17},
-    {0.5059288537549407, 0.6813592248079031, 1.7765482243852914e-17},
-    {0.5039370078740157, 0.6853040030989195, -4.8209665191998585e-17},
-    {0.5019607843137255, 0.689233281238809, -9.330006029414747e-18},
-    {0.5, 0.6931471805599453, 2.3190468138462996e-17}
-};
-
-__device__ __noinline__ double log_outside(double x) { return log(x); }
-
-__device__ __forceinline__ double xlog(double x) {
-  const int hx = __double2hiint(x);
-  if (hx < 0x00100000 || hx >= 0x7ff00000) return log_outside(x);
-  constexpr double kLn2Hi = 0.6931467056274414;      // ln 2 with the low 32 mantissa bits cleared
-  constexpr double kLn2Lo = 4.7493250390316726e-07;  // ln 2 - kLn2Hi
-  const int mb = hx & 0x000fffff;
-  const int j = (mb + 0x1000) >> 13;
-  const double y = __hiloint2double(mb | 0x3ff00000, __double2loint(x));
-  const double* e = g_log_tab[j];
-  const double r = fma(y, __ldg(e), -1.0);
-  double q = fma(r, 1.0 / 7.0, -1.0 / 6.0);
-  q = fma(r, q, 1.0 / 5.0);
-  q = fma(r, q, -0.25);
-  q = fma(r, q, 1.0 / 3.0);
-  q = fma(r, q, -0.5);
-  const double l1p = fma(r * r, q, r);  // ln(1 + r)
-  const double md = (double)((hx >> 20) - 1023);
-  const double t = fma(md, kLn2Hi, __ldg(e + 1));
-  return t + fma(md, kLn2Lo, __ldg(e + 2) + l1p);
-}
-
-// 1/x by Newton's iteration r <- r + r (1 - x r) from the hardware's approximate
-// reciprocal (two steps take its error below one ulp); magnitudes outside
-// [2^-1000, 2^1000], zero, infinities and NaN take the IEEE division.
-__device__ __forceinline__ double xrcp(double x) {
-  const int ex = (__double2hiint(x) >> 20) & 0x7ff;
-  if (ex < 23 || ex > 2023) return 1.0 / x;
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
-}
-
-
-// Precision policy: LU = type of the factorised matrix, ASM = type the Jacobian is
-// assembled in; IR = refine each solve against the assembled matrix.
-template <int PREC>
-struct Policy {
-  using LU = double;
-  using ASM = double;
-  static constexpr bool IR = false;
-};
-template <>
-struct Policy<PREC_MIXED> {
-  using LU = float;
-  using ASM = double;
-  static constexpr bool IR = true;
-};
-template <>
-struct Policy<PREC_FP32ASM> {
-  using LU = float;
-  using ASM = float;
-  static constexpr bool IR = true;
-};
-
-// ---------------------------------------------------------------------------
-// shared-memory carve-up
-// ---------------------------------------------------------------------------
-struct Layout {
-  int nmax, ld;            // matrix dimension bound and leading dimension (odd)
-  int Kmax, Imax;
-  size_t off_vec, off_sp, off_rx, off_M, off_M0, off_piv, off_red, off_tab, total;
-};
-
-__host__ __device__ inline int odd_ld(int n) { return n | 1; }
-
-// vectors (double): y, yn, ys, f0, fv, rr, u[6], sc  -> 13 n
-// species (double): C, hRT, cpR, eg, dcp, dk, akT, ek, ieg -> 9 K
-// reactions (double): q, D, dTc, P, dqs[4] -> 8 I
-// m0_global: the mixed form's FP64 assembled matrix lives in a global-memory slot of
-// the CTA instead of shared memory (large mechanisms, persistent schedulers).
-__host__ __device__ inline Layout make_layout(int Kmax, int Imax, int prec, bool m0_global = false) {
-  Layout L;
-  L.nmax = Kmax + 1;
-  L.ld = odd_ld(L.nmax);
-  L.Kmax = Kmax;
-  L.Imax = Imax;
-  size_t o = 0;
-  L.off_red = o;
-  o += 64 * sizeof(double);
-  L.off_tab = o;  // the exponential's table (copied from g_exp2_tab at kernel start)
-  o += 32 * sizeof(double2);
-  L.off_vec = o;
-  o += (size_t)13 * L.nmax * sizeof(double);
-  L.off_sp = o;
-  o += (size_t)9 * Kmax * sizeof(double);
-  L.off_rx = o;
-  if (prec == PREC_FP64) {
-    o += (size_t)8 * Imax * sizeof(double);
-    L.off_M = o;
-    o += (size_t)L.nmax * L.ld * sizeof(double);
-  } else {
-    // The FP32 factor matrix is written only after the assembly has consumed the
-    // per-reaction Jacobian data (everything after q), so it shares their space.
-    L.off_M = o + (size_t)Imax * sizeof(double);
-    const size_t jac = (size_t)7 * Imax * sizeof(double);
-    const size_t mat = (size_t)L.nmax * L.ld * sizeof(float);
-    o += (size_t)Imax * sizeof(double) + (jac > mat ? jac : mat);
-  }
-  o = (o + 15) & ~(size_t)15;
-  L.off_M0 = o;
-  if (prec == PREC_MIXED && !m0_global) o += (size_t)L.nmax * L.ld * sizeof(double);
-  if (prec == PREC_FP32ASM) o += (size_t)L.nmax * L.ld * sizeof(float);
-  o = (o + 15) & ~(size_t)15;
-  L.off_piv = o;
-  o += (size_t)2 * L.nmax * sizeof(int);  // pivots, permutation
-  o += (size_t)L.nmax * sizeof(double);   // inverse diagonal of U
-  o = (o + 15) & ~(size_t)15;
-  L.total = o;
-  return L;
-}
 
 size_t smem_bytes(int Kmax, int Imax, int prec, bool m0_global) {
   return make_layout(Kmax, Imax, prec, m0_global).total;
 }
 
-// Scalars kept in the reduction area (after the 4 x NW partial-sum slots).
-// SC_OUT: 8 broadcast results of Cta::reduce; SC_PIV: pivot search slots (12 NW bytes)
-// (SC_INVT during the rate evaluation, SC_INVP during the LU: never live together)
-enum { SC_OUT = 32, SC_LOGT = 48, SC_INVT = 49, SC_INVP = 49, SC_FLAG = 50, SC_MISC = 51, SC_PIV = 52 };
-
-template <int NW>
-struct Cta {
-  static constexpr int NT = NW * 32;
-  static constexpr int SW = NW - 1;  // the warp that finishes reductions and CTA scalars
-  int tid, lane, warp;
-  double* red;
-  // vectors
-  double *y, *yn, *ys, *f0, *fv, *rr, *u, *sc;
-  // species
-  double *C, *hRT, *cpR, *eg, *dcp, *dk, *akT, *ek, *ieg;
-  // reactions
-  double *q, *D, *dTc, *P, *dqs;
-  void* M;
-  void* M0;
-  int *piv, *perm;
-  double* invd;
-  double2* etab;
-
-  __device__ void bind(unsigned char* base, const Layout& L) {
-    tid = threadIdx.x;
-    lane = tid & 31;
-    warp = tid >> 5;
-    red = reinterpret_cast<double*>(base + L.off_red);
-    double* v = reinterpret_cast<double*>(base + L.off_vec);
-    const int n = L.nmax;
-    y = v;
-    yn = v + n;
-    ys = v + 2 * n;
-    f0 = v + 3 * n;
-    fv = v + 4 * n;
-    rr = v + 5 * n;
-    u = v + 6 * n;   // 6 n
-    sc = v + 12 * n;
-    double* s = reinterpret_cast<double*>(base + L.off_sp);
-    const int K = L.Kmax;
-    C = s;
-    hRT = s + K;
-    cpR = s + 2 * K;
-    eg = s + 3 * K;
-    dcp = s + 4 * K;
-    dk = s + 5 * K;
-    akT = s + 6 * K;
-    ek = s + 7 * K;
-    ieg = s + 8 * K;
-    double* r = reinterpret_cast<double*>(base + L.off_rx);
-    const int I = L.Imax;
-    q = r;
-    D = r + I;
-    dTc = r + 2 * I;
-    P = r + 3 * I;
-    dqs = r + 4 * I;
-    M = base + L.off_M;
-    M0 = base + L.off_M0;
-    piv = reinterpret_cast<int*>(base + L.off_piv);
-    perm = piv + L.nmax;
-    invd = reinterpret_cast<double*>(perm + L.nmax);
-    etab = reinterpret_cast<double2*>(base + L.off_tab);
-  }
-
-  // copy the exponential's table to shared memory (visible after the next barrier)
-  __device__ void load_tables() {
-    for (int i = tid; i < 32; i += NT) etab[i] = g_exp2_tab[i];
-  }
-
-  // Sum of NV values over the CTA; every thread receives the same totals
-  // (fixed summation order: deterministic). Only the first nw warps may hold
-  // non-zero values (the others skip the shuffle tree). The last warp (SW, which
-  // holds no species in the usual case of fewer species than threads) adds the
-  // per-warp partials and passes the totals to fin(tot, out), which derives NO
-  // scalars from them; lane 0's out[] reaches every thread through shared memory,
-  // so scalar follow-up work (reciprocals, roots) runs on one warp, not all.
-  template <int NV, int NO, class F>
-  __device__ void reduce(const double (&v)[NV], int nw, F fin, double (&out)[NO]) {
-    static_assert(NV * NW <= SC_OUT && NO <= 8, "reduction slots");
-    if (warp < nw) {
-#pragma unroll
-      for (int a = 0; a < NV; ++a) {
-        double x = v[a];
-#pragma unroll
-        for (int o = 16; o; o >>= 1) x += __shfl_down_sync(FULLMASK, x, o);
-        if (lane == 0) red[a * NW + warp] = x;
-      }
-    }
-    __syncthreads();
-    if (warp == SW) {
-      double tot[NV];
-#pragma unroll
-      for (int a = 0; a < NV; ++a) {
-        double s = red[a * NW];
-        for (int w = 1; w < nw; ++w) s += red[a * NW + w];
-        tot[a] = s;
-      }
-      double o[NO];
-      fin(tot, o);
-      if (lane == 0) {
-#pragma unroll
-        for (int b = 0; b < NO; ++b) red[SC_OUT + b] = o[b];
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int b = 0; b < NO; ++b) out[b] = red[SC_OUT + b];
-  }
-
-  // Plain CTA sum of NV values (nw as in reduce).
-  template <int NV>
-  __device__ void sum(double (&v)[NV], int nw = NW) {
-    reduce(v, nw, [](const double (&t)[NV], double (&o)[NV]) {
-#pragma unroll
-      for (int a = 0; a < NV; ++a) o[a] = t[a];
-    }, v);
-  }
-};
-
-// number of warps that hold data in a loop `for (i = tid; i < count; i += NT)`
-template <int NW>
-__device__ __forceinline__ int warps_for(int count) {
-  const int w = (count + 31) >> 5;
-  return w < NW ? w : NW;
-}
-
-// Cell-level scalars shared by all threads of the CTA (identical in every thread).
-struct Scal {
-  double T, invT, logT, rho, irho, Wbar, cpm, icpm, fT, dcpm, Scpw;
-};
-
-// ---------------------------------------------------------------------------
-// thermo, rates, RHS and the per-reaction Jacobian data
-// ---------------------------------------------------------------------------
-// RHS of y = [T, Y] at constant p into f[0..K]. With JAC, also the data the
-// Jacobian assembly needs: per reaction the slot derivatives dq/dC, dq/dT at
-// fixed C, sum_k C_k dq/dC_k (D), and the third-body/falloff coefficient P of
-// eff_j in dq/dC_j; per species d_k = sum_i nu_ki D_i and a_kT = sum nu dTc.
-template <int NW, bool JAC, bool FF = false>
-__device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p, double* f) {
-  constexpr int NT = NW * 32;
-  const int K = m.K;
-  Scal s;
-  s.T = y[0];
-  // the scalar warp: ln T and 1/T for every thread (read after the reduction's barriers)
-  double invT0 = 0.0;
-  if (c.warp == Cta<NW>::SW) {
-    const double lg = xlog(s.T);
-    invT0 = xrcp(s.T);
-    if (c.lane == 0) {
-      c.red[SC_LOGT] = lg;
-      c.red[SC_INVT] = invT0;
-      c.red[SC_FLAG] = 0.0;  // set below when some |G/RT| is too large for the factor products
-    }
-  }
-  {
-    double part[1] = {0.0};
-    for (int k = c.tid; k < K; k += NT) part[0] += y[1 + k] * m.invW[k];
-    double o[3];
-    const double T = s.T;
-    c.reduce(part, warps_for<NW>(K), [&](const double (&t)[1], double (&r)[3]) {
-      const double Wbar = xrcp(t[0]);
-      r[0] = Wbar;
-      r[1] = p * invT0 * Wbar * (1.0 / kRc);  // rho = p Wbar / (Rc T)
-      r[2] = kRc * T * t[0] / p;              // 1 / rho
-    }, o);
-    s.Wbar = o[0];
-    s.rho = o[1];
-    s.irho = o[2];
-  }
-  s.logT = c.red[SC_LOGT];
-  s.invT = c.red[SC_INVT];
-  const double T = s.T, invT = s.invT, logT = s.logT;
-  // species: thermo, exp(G/RT), concentrations
-  for (int k = c.tid; k < K; k += NT) {
-    const double* a = m.nasa + 36 * k;
-    a += (T < a[34]) ? 0 : 17;
-    double cp = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
-    double h = a[5] + T * (a[6] + T * (a[7] + T * (a[8] + T * a[9]))) + a[10] * invT;
-    double sr = a[11] * logT + T * (a[12] + T * (a[13] + T * (a[14] + T * a[15]))) + a[16];
-    c.cpR[k] = cp;
-    c.hRT[k] = h;
-    const double g = h - sr;
-    const double e = xexp(g, c.etab);
-    c.eg[k] = e;
-    c.ieg[k] = xrcp(e);
-    c.ek[k] = g;  // G/RT (the slot is the Jacobian assembly's, unused until then)
-    if (fabs(g) > kBigGRT) c.red[SC_FLAG] = 1.0;
-    const double Ck = s.rho * y[1 + k] * m.invW[k];
-    c.C[k] = Ck;
-    // float-float copy of C for the third-body sums (the slot of d_k, which the
-    // Jacobian evaluation writes only after the reaction loop)
-    if (FF) reinterpret_cast<ff2*>(c.dk)[k] = ff_split(Ck);
-    if (JAC) c.dcp[k] = a[1] + T * (2.0 * a[2] + T * (3.0 * a[3] + T * 4.0 * a[4]));
-  }
-  __syncthreads();
-  const double cRT = kRc * T / kP0;  // (P0 / (Rc T))^-1
-  const double icRT = kP0 * invT / kRc;
-  // A cell with some |G/RT| > kBigGRT (very low T with large formation enthalpies)
-  // takes one exponential of the summed exponent per reaction instead of the product
-  // of four species factors, whose partial products could overflow or underflow.
-  const bool bigG = c.red[SC_FLAG] != 0.0;
-  // 32-reaction chunks of one kind each, dealt to the warps by estimated work
-  const int* cs = m.chunk_sched[NW == 2 ? 0 : NW == 4 ? 1 : 2];
-  for (int pos = cs[c.warp]; pos < cs[c.warp + 1]; ++pos) {
-    const int i = cs[NW + 1 + pos] * 32 + c.lane;
-    const int4 sl = m.slots[i];
-    if (sl.x < 0) {  // null padding reaction
-      c.q[i] = 0.0;
-      if (JAC) {
-        c.D[i] = c.dTc[i] = c.P[i] = 0.0;
-        c.dqs[4 * i] = c.dqs[4 * i + 1] = c.dqs[4 * i + 2] = c.dqs[4 * i + 3] = 0.0;
-      }
-      continue;
-    }
-    const double* arp = m.arr + 4 * i;
-    const double2 a01 = reinterpret_cast<const double2*>(arp)[0];
-    const double2 a23 = reinterpret_cast<const double2*>(arp)[1];
-    const struct { double x, y, z, w; } ar = {a01.x, a01.y, a23.x, a23.y};
-    double kf = xexp(ar.x + ar.y * logT - ar.z * invT, c.etab);
-    const double Ca = c.C[sl.x];
-    const double Cb = sl.y >= 0 ? c.C[sl.y] : 1.0;
-    const double Cc = c.C[sl.z];
-    const double Cd = sl.w >= 0 ? c.C[sl.w] : 1.0;
-    const double Pf = Ca * Cb, Pb = Cc * Cd;
-    // 1/Kc = exp(dG/RT) (Rc T/P0)^dnu with exp(dG/RT) from the species factors
-    double ratio = 0.0;
-    const int rv = m.rev[i];
-    if (rv & 1) {
-      if (!bigG) {
-        ratio = c.eg[sl.z] * c.ieg[sl.x];
-        if (sl.w >= 0) ratio *= c.eg[sl.w];
-        if (sl.y >= 0) ratio *= c.ieg[sl.y];
-        ratio *= (rv >> 1) == 2 ? cRT : (rv >> 1) == 0 ? icRT : 1.0;
-      } else {
-        double dg = c.ek[sl.z] - c.ek[sl.x];
-        if (sl.w >= 0) dg += c.ek[sl.w];
-        if (sl.y >= 0) dg -= c.ek[sl.y];
-        const double lc = logT + kLnRcP0;  // ln(Rc T / P0)
-        dg += (rv >> 1) == 2 ? lc : (rv >> 1) == 0 ? -lc : 0.0;
-        ratio = xexp(dg, c.etab);
-      }
-    }
-    double Mc = 0.0, phi = 1.0;
-    double dk_dM = 0.0, dlnk = (ar.y + ar.z * invT) * invT, dk_dT = 0.0;
-    if (i >= m.i_tb0) {
-      const double* e = m.eff + (size_t)(i - m.i_tb0) * K;
-      if (FF) {
-        const ff2* ef = m.eff_ff + (size_t)(i - m.i_tb0) * K;
-        const ff2* Cf = reinterpret_cast<const ff2*>(c.dk);
-        ff2 acc = {0.0f, 0.0f};
-        for (int k = 0; k < K; ++k) acc = ff_add(acc, ff_mul(ef[k], Cf[k]));
-        Mc = ff_value(acc);
-      } else {
-        for (int k = 0; k < K; ++k) Mc += e[k] * c.C[k];
-      }
-      if (i < m.i_fo0) phi = Mc;
-    }
-    if (i >= m.i_fo0) {
-      // fo[0..2] hold the low-pressure minus the high-pressure Arrhenius parameters,
-      // so one exponential gives k0 / kinf
-      const double* fo = m.fo + 8 * (i - m.i_fo0);
-      const double r0 = xexp(fo[0] + fo[1] * logT - fo[2] * invT, c.etab);  // k0 / kinf
-      const double Pr = r0 * Mc;
-      double F = 1.0, dlgF_dL = 0.0, dlnF_dT = 0.0;
-      if (i >= m.i_troe0) {
-        const double alpha = fo[3];
-        // fo[4] = 1/T***, fo[5] = 1/T*
-        const double e3 = xexp(-T * fo[4], c.etab), e1 = xexp(-T * fo[5], c.etab);
-        double Fc = (1.0 - alpha) * e3 + alpha * e1;
-        double dFc = -(1.0 - alpha) * fo[4] * e3 - alpha * fo[5] * e1;
-        if (fo[6] > 0.0) {
-          const double e2 = xexp(-fo[6] * invT, c.etab);
-          Fc += e2;
-          dFc += fo[6] * invT * invT * e2;
-        }
-        const double lF = xlog(Fc) * kInvLn10;
-        const double cc = -0.4 - 0.67 * lF, nn = 0.75 - 1.27 * lF;
-        const double x = xlog(Pr) * kInvLn10 + cc;
-        const double iden = xrcp(nn - 0.14 * x);
-        const double f1 = x * iden;
-        const double ig = xrcp(fma(f1, f1, 1.0));
-        const double lgF = lF * ig;
-        F = xexp(lgF * 2.302585092994046, c.etab);  // 10^lgF
-        if (JAC) {
-          // partial derivatives of log10 F by log10 Pr and by log10 Fc
-          const double df1_dL = nn * iden * iden;
-          const double df1_dlF = (-0.67 - f1 * (-1.27 + 0.14 * 0.67)) * iden;
-          dlgF_dL = -2.0 * lgF * ig * f1 * df1_dL;
-          const double dlgF_dlF = ig - 2.0 * lgF * ig * f1 * df1_dlF;
-          dlnF_dT = dlgF_dlF * dFc * xrcp(Fc);  // d ln F / dT at fixed Pr
-        }
-      }
-      const double red1 = xrcp(1.0 + Pr);
-      const double kinf = kf;
-      kf = kinf * Pr * red1 * F;
-      if (JAC) {
-        // d ln k / d ln Pr = 1/(1 + Pr) + d log10 F / d log10 Pr; Pr = (k0/kinf) [M]
-        const double g = red1 + dlgF_dL;
-        dk_dM = kinf * red1 * F * g * r0;
-        dk_dT = kf * (dlnk + g * (fo[1] + fo[2] * invT) * invT + dlnF_dT);
-      }
-    }
-    const double kr = kf * ratio;
-    const double net = kf * Pf - kr * Pb;
-    c.q[i] = phi * net;
-    if (JAC) {
-      // d ln Kc / dT = dH/(R T^2) - dnu/T
-      double dH = c.hRT[sl.z] + (sl.w >= 0 ? c.hRT[sl.w] : 0.0) - c.hRT[sl.x] -
-                  (sl.y >= 0 ? c.hRT[sl.y] : 0.0);
-      const double dlnKc = (dH - ar.w) * invT;
-      double* dq = c.dqs + 4 * i;
-      dq[0] = phi * kf * Cb;
-      dq[1] = sl.y >= 0 ? phi * kf * Ca : 0.0;
-      dq[2] = -phi * kr * Cd;
-      dq[3] = sl.w >= 0 ? -phi * kr * Cc : 0.0;
-      double Dsum = Ca * dq[0] + (sl.y >= 0 ? Cb * dq[1] : 0.0) + Cc * dq[2] + (sl.w >= 0 ? Cd * dq[3] : 0.0);
-      double dtc, Pc;
-      if (i >= m.i_fo0) {
-        const double netc = Pf - ratio * Pb;
-        dtc = dk_dT * netc + ((rv & 1) ? kr * Pb * dlnKc : 0.0);
-        Pc = dk_dM * netc;
-      } else {
-        const double dkf = kf * dlnk;
-        const double dkr = kr * (dlnk - dlnKc);
-        dtc = phi * (dkf * Pf - dkr * Pb);
-        Pc = (i >= m.i_tb0) ? net : 0.0;
-      }
-      if (i >= m.i_tb0) Dsum += Mc * Pc;
-      c.dTc[i] = dtc;
-      c.P[i] = Pc;
-      c.D[i] = Dsum;
-    }
-  }
-  __syncthreads();
-  // species: production rates, f_k, enthalpy and heat-capacity sums
-  double part[JAC ? 4 : 2];
-  part[0] = part[1] = 0.0;
-  if (JAC) part[2] = part[3] = 0.0;
-  for (int k = c.tid; k < K; k += NT) {
-    double w = 0.0, dd = 0.0, at = 0.0;
-    for (int e = m.sp_ptr[k]; e < m.sp_ptr[k + 1]; ++e) {
-      const int2 en = m.sp_ent[e];
-      const double nu = m.sp_nu[e];
-      w += nu * c.q[en.x];
-      if (JAC) {
-        dd += nu * c.D[en.x];
-        at += nu * c.dTc[en.x];
-      }
-    }
-    f[1 + k] = m.W[k] * w * s.irho;
-    part[0] += c.hRT[k] * w;                  // Qh / (Rc T)
-    part[1] += y[1 + k] * c.cpR[k] * m.invW[k];  // cpm / Rc
-    if (JAC) {
-      c.dk[k] = dd;
-      c.akT[k] = at;
-      part[2] += y[1 + k] * c.dcp[k] * m.invW[k];  // dcpm/dT / Rc
-      part[3] += c.cpR[k] * w;                      // sum cp_k omega_k / Rc
-    }
-  }
-  {
-    double o[5];
-    const double T = s.T, irho = s.irho;
-    c.reduce(part, warps_for<NW>(K), [&](const double (&t)[JAC ? 4 : 2], double (&r)[5]) {
-      const double cpm = kRc * t[1];
-      const double icpm = xrcp(cpm);
-      const double fT = -kRc * T * t[0] * irho * icpm;  // -Qh / (rho cp), Qh = Rc T sum hRT_k w_k
-      r[0] = cpm;
-      r[1] = icpm;
-      r[2] = fT;
-      if constexpr (JAC) {
-        r[3] = kRc * t[2];
-        r[4] = kRc * t[3];
-      } else {
-        r[3] = r[4] = 0.0;
-      }
-      if (c.lane == 0) f[0] = fT;  // visible after the reduction's last barrier
-    }, o);
-    s.cpm = o[0];
-    s.icpm = o[1];
-    s.fT = o[2];
-    s.dcpm = o[3];
-    s.Scpw = o[4];
-  }
-  return s;
-}
-
-// ---------------------------------------------------------------------------
-// Jacobian assembly (precision R) from the data of eval_rhs<JAC=true>.
-// With A_kj = sum_i nu_ki dq_i/dC_j (mass-action slot terms plus the third-body /
-// falloff term nu_ki P_i eff_ij), the species rows of the Jacobian are
-//   J_kj = (W_k / W_j) (A_kj - (Wbar/rho) d_k) + f_k Wbar / W_j,
-// so with sg = -1 for the iteration matrix M = I/(h gamma) - J (rf = 1/(h gamma))
-// and sg = +1, rf = 0 for the Jacobian itself (JO), the stored value is
-//   S_kj = B_kj / W_j + rf delta_kj,  B_kj = sg W_k A_kj + beta_k,
-//   beta_k = sg (f_k Wbar - W_k (Wbar/rho) d_k).
-// (1) species pass: e_k = h_k / (W_k cp), beta_k, the temperature column
-//     J_k0 = (W_k/rho)(a_kT - d_k/T) + f_k/T; and the mass-action pair sums
-//     sum sg nu_ki W_k dq_i/dC_j on the thread-balanced schedule, stored in place;
-// (2) one warp per row: beta + pair sum, the dense third-body part in registers
-//     (lane l holds columns l + 32 u), scaled by 1/W_j;
-// (3) temperature row from column sums of the stored rows:
-//     J_0j = -sum_k e_k J_kj - f_T cp_j/(W_j cp),
-//     J_00 = -sum_k e_k J_k0 - sum_k cp_k omega_k/(rho cp) - f_T cp'/cp.
-// ---------------------------------------------------------------------------
-template <class R>
-__device__ __forceinline__ R fmaR(R a, R b, R c) {
-  if constexpr (std::is_same<R, float>::value) return fmaf(a, b, c);
-  else return fma(a, b, c);
-}
-
-template <int NW, class R, bool JO, int U>
-__device__ void assemble_rows(const DevMech& m, Cta<NW>& c, R* A, int K, int ld, R rf) {
-  constexpr double SG = JO ? 1.0 : -1.0;
-  for (int k = c.warp; k < K; k += NW) {
-    R* row = A + (1 + k) * ld + 1;
-    const R beta = R(c.akT[k]);
-    R acc[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const unsigned msk = m.jmask[k * U + u];
-      acc[u] = ((msk >> c.lane) & 1u) ? beta + row[c.lane + 32 * u] : beta;
-    }
-    // third-body / falloff part: 32 row coefficients sg nu_ki W_k P_i at a time,
-    // broadcast from their lanes
-    const int t1 = m.tr_ptr[k + 1];
-    for (int tb = m.tr_ptr[k]; tb < t1; tb += 32) {
-      const int t = tb + c.lane;
-      R cl = R(0);
-      int rl = 0;
-      if (t < t1) {
-        const int ri = m.tr_ent[t].x;
-        cl = R(SG * m.tr_nu[t] * c.P[ri]);
-        rl = ri - m.i_tb0;
-      }
-      const int cnt = min(32, t1 - tb);
-      for (int q = 0; q < cnt; ++q) {
-        const R coef = __shfl_sync(FULLMASK, cl, q);
-        const double* e = m.eff + (size_t)__shfl_sync(FULLMASK, rl, q) * K;
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int j = c.lane + 32 * u;
-          if (u < U - 1 || j < K) acc[u] = fmaR(coef, R(e[j]), acc[u]);
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int j = c.lane + 32 * u;
-      if (u < U - 1 || j < K) row[j] = fmaR(acc[u], R(m.invW[j]), j == k ? rf : R(0));
-    }
-  }
-}
-
-template <int NW, class R, bool JO>
-__device__ void assemble(const DevMech& m, Cta<NW>& c, const Scal& s, const double* f, double fac, void* target) {
-  constexpr int NT = NW * 32;
-  constexpr double SG = JO ? 1.0 : -1.0;
-  const int K = m.K, n = K + 1, ld = odd_ld(n);
-  R* A = reinterpret_cast<R*>(target);
-  const R rf = JO ? R(0) : R(fac);
-  // (1) species pass
-  const double eT = kRc * s.T * s.icpm, wr = s.Wbar * s.irho;
-  for (int k = c.tid; k < K; k += NT) {
-    c.ek[k] = c.hRT[k] * eT * m.invW[k];
-    const double Wk = m.W[k], dk = c.dk[k], fk = f[1 + k];
-    A[(1 + k) * ld] = R(SG * (Wk * s.irho * (c.akT[k] - dk * s.invT) + fk * s.invT));
-    c.akT[k] = SG * (fk * s.Wbar - Wk * wr * dk);  // beta_k (a_kT is consumed)
-  }
-  {
-    const int v = NT == 64 ? 0 : NT == 128 ? 1 : 2;
-    const int2* se = m.js_ent[v] + c.tid;
-    const double* sn = m.js_nu[v] + c.tid;
-    const int rounds = m.js_rounds[v];
-    R a = R(0);
-    for (int r = 0; r < rounds; ++r) {
-      const int2 e = se[r * NT];
-      if (e.x >= 0) a = fmaR(R(SG * sn[r * NT]), R(c.dqs[e.x]), a);
-      if (e.y >= 0) {
-        A[e.y] = a;
-        a = R(0);
-      }
-    }
-  }
-  __syncthreads();
-  // (2) species rows
-  switch ((K + 31) >> 5) {
-    case 1: assemble_rows<NW, R, JO, 1>(m, c, A, K, ld, rf); break;
-    case 2: assemble_rows<NW, R, JO, 2>(m, c, A, K, ld, rf); break;
-    case 3: assemble_rows<NW, R, JO, 3>(m, c, A, K, ld, rf); break;
-    case 4: assemble_rows<NW, R, JO, 4>(m, c, A, K, ld, rf); break;
-    case 5: assemble_rows<NW, R, JO, 5>(m, c, A, K, ld, rf); break;
-    case 6: assemble_rows<NW, R, JO, 6>(m, c, A, K, ld, rf); break;
-    case 7: assemble_rows<NW, R, JO, 7>(m, c, A, K, ld, rf); break;
-    default: assemble_rows<NW, R, JO, 8>(m, c, A, K, ld, rf); break;
-  }
-  __syncthreads();
-  // (3) temperature row; with acc = sum_k e_k S_kj, sum_k e_k J_kj = sg (acc - rf e_(j-1)),
-  //     so S_0j = rf e_(j-1) - acc - sg extra_j (j >= 1) and S_00 = rf - acc - sg extra_0
-  const double ft = s.fT * s.icpm;
-  for (int j = NT - 1 - c.tid; j < n; j += NT) {  // from the last warp down, as the residual rows
-    R acc = R(0);
-    for (int k = 0; k < K; ++k) acc = fmaR(R(c.ek[k]), A[(1 + k) * ld + j], acc);
-    R v;
-    if (j == 0)
-      v = rf - acc - R(SG * (s.Scpw * s.irho * s.icpm + ft * s.dcpm));
-    else
-      v = rf * R(c.ek[j - 1]) - acc - R(SG * ft * c.cpR[j - 1] * kRc * m.invW[j - 1]);
-    A[j] = v;
-  }
-  __syncthreads();
-}
-
-// ---------------------------------------------------------------------------
-// Pivot candidates: every warp writes (max |value|, lowest row index) of its rows;
-// every thread then reduces the NW partials in the same order (same result).
-// ---------------------------------------------------------------------------
-template <int NW>
-__device__ __forceinline__ int pivot_reduce(Cta<NW>& c, float* pmax, int* pidx, int n) {
-  float best = -1.0f;
-  int bi = n;
-#pragma unroll
-  for (int w = 0; w < NW; ++w) {
-    const float v = pmax[w];
-    const int i = pidx[w];
-    if (v > best || (v == best && i < bi)) { best = v; bi = i; }
-  }
-  return bi;
-}
-
-// Warp-level (value, index) maximum with the lowest index on ties; lane 0 stores it.
-__device__ __forceinline__ void warp_argmax_store(float v, int i, int lane, float* pmax, int* pidx, int warp) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    const float ov = __shfl_xor_sync(FULLMASK, v, o);
-    const int oi = __shfl_xor_sync(FULLMASK, i, o);
-    if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
-  }
-  if (lane == 0) {
-    pmax[warp] = v;
-    pidx[warp] = i;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// dense LU with partial pivoting (row interchange to the largest |a_ik|, lowest
-// row index on ties; the pivot choice compares magnitudes rounded to FP32), in
-// place; the search for the next pivot is fused into the elimination, so each
-// column costs two CTA barriers. Then the composed row permutation and the
-// inverse diagonal of U for the solves. Returns 0 or 1 + k for a zero pivot.
-// ---------------------------------------------------------------------------
-template <int NW, class R>
-__device__ int lu_factor(Cta<NW>& c, R* a, int n, bool pivot = true) {
-  constexpr int NT = NW * 32;
-  const int ld = odd_ld(n);
-  float* pmax = reinterpret_cast<float*>(c.red + SC_PIV);
-  int* pidx = reinterpret_cast<int*>(c.red + SC_PIV + NW);
-  double* spinv = c.red + SC_INVP;
-  int info = 0;
-  // candidates for column 0
-  {
-    float v = -1.0f;
-    int bi = n;
-    for (int i = c.tid; i < n; i += NT) {
-      const float x = fabsf((float)a[i * ld]);
-      if (x > v || (x == v && i < bi)) { v = x; bi = i; }
-    }
-    warp_argmax_store(v, bi, c.lane, pmax, pidx, c.warp);
-  }
-  __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    int p = pivot ? pivot_reduce<NW>(c, pmax, pidx, n) : k;  // no pivoting: the diagonal
-    if (p >= n) p = k;  // a column of NaN: the zero-pivot path below
-    if (c.tid == 0) {
-      c.piv[k] = p;
-      const double pv = (double)a[p * ld + k];
-      spinv[0] = pv != 0.0 && isfinite(pv) ? 1.0 / pv : 0.0;
-    }
-    if (p != k)
-      for (int j = c.tid; j < n; j += NT) {
-        const R t = a[k * ld + j];
-        a[k * ld + j] = a[p * ld + j];
-        a[p * ld + j] = t;
-      }
-    __syncthreads();
-    const R invp = R(spinv[0]);
-    if (invp == R(0) && info == 0) info = k + 1;
-    float v = -1.0f;
-    int bi = n;
-    for (int i = k + 1 + c.warp; i < n; i += NW) {
-      const R l = a[i * ld + k] * invp;
-      __syncwarp();
-      if (c.lane == 0) a[i * ld + k] = l;
-      for (int j = k + 1 + c.lane; j < n; j += 32) {
-        const R nv = a[i * ld + j] - l * a[k * ld + j];
-        a[i * ld + j] = nv;
-        if (j == k + 1) {
-          const float x = fabsf((float)nv);
-          if (x > v || (x == v && i < bi)) { v = x; bi = i; }
-        }
-      }
-    }
-    warp_argmax_store(v, bi, c.lane, pmax, pidx, c.warp);
-    __syncthreads();
-  }
-  // composed permutation: position i of the pivoted system holds original row perm[i]
-  if (c.tid == 0) {
-    for (int i = 0; i < n; ++i) c.perm[i] = i;
-    for (int k = 0; k < n; ++k) {
-      const int p = c.piv[k];
-      const int t = c.perm[k];
-      c.perm[k] = c.perm[p];
-      c.perm[p] = t;
-    }
-  }
-  for (int i = c.tid; i < n; i += NT) c.invd[i] = 1.0 / (double)a[i * ld + i];
-  __syncthreads();
-  return info;
-}
-
-// Forward/back substitution by one warp, in place on x (already permuted).
-template <class R>
-__device__ void lu_solve_warp(const R* a, int n, const double* invd, R* x, int lane) {
-  const int ld = odd_ld(n);
-  for (int i0 = 0; i0 < n; i0 += 32) {
-    const int i = i0 + lane;
-    const int jend = min(i0 + 32, n);
-    R xi = i < n ? x[i] : R(0);
-    for (int j = i0; j < jend; ++j) {
-      const R xj = __shfl_sync(FULLMASK, xi, j - i0);
-      if (i > j && i < n) xi -= a[i * ld + j] * xj;
-    }
-    if (i < n) x[i] = xi;
-    __syncwarp();
-    for (int r = i0 + 32 + lane; r < n; r += 32) {
-      R sacc = R(0);
-      for (int j = i0; j < jend; ++j) sacc += a[r * ld + j] * x[j];
-      x[r] -= sacc;
-    }
-    __syncwarp();
-  }
-  for (int i1 = n; i1 > 0; i1 -= 32) {
-    const int i0 = max(0, i1 - 32);
-    const int i = i0 + lane;
-    R xi = i < i1 ? x[i] : R(0);
-    for (int j = i1 - 1; j >= i0; --j) {
-      if (i == j) xi *= R(invd[j]);
-      const R xj = __shfl_sync(FULLMASK, xi, j - i0);
-      if (i < j) xi -= a[i * ld + j] * xj;
-    }
-    if (i < i1) x[i] = xi;
-    __syncwarp();
-    for (int r = lane; r < i0; r += 32) {
-      R sacc = R(0);
-      for (int j = i0; j < i1; ++j) sacc += a[r * ld + j] * x[j];
-      x[r] -= sacc;
-    }
-    __syncwarp();
-  }
-}
-
-// In-place Gauss-Jordan inverse (FP32) with partial pivoting: row interchange to
-// the largest |a_ik| (lowest row index on ties), the normalised pivot row kept in a
-// copy while every other row is eliminated (the next pivot search is fused into
-// that elimination: two CTA barriers per column); the inverse is completed by the
-// column interchanges in reverse order. Returns 0 or 1 + k for a zero pivot.
-template <int NW>
-__device__ int gj_invert(Cta<NW>& c, float* a, int n) {
-  constexpr int NT = NW * 32;
-  const int ld = odd_ld(n);
-  float* pmax = reinterpret_cast<float*>(c.red + SC_PIV);
-  int* pidx = reinterpret_cast<int*>(c.red + SC_PIV + NW);
-  float* pr = reinterpret_cast<float*>(c.rr);  // normalised pivot row
-  int info = 0;
-  {
-    float v = -1.0f;
-    int bi = n;
-    for (int i = c.tid; i < n; i += NT) {
-      const float x = fabsf(a[i * ld]);
-      if (x > v || (x == v && i < bi)) { v = x; bi = i; }
-    }
-    warp_argmax_store(v, bi, c.lane, pmax, pidx, c.warp);
-  }
-  __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    int p = pivot_reduce<NW>(c, pmax, pidx, n);
-    if (p >= n) p = k;
-    const float pv = a[p * ld + k];
-    const float pinv = (pv != 0.0f && isfinite(pv)) ? 1.0f / pv : 0.0f;
-    if (pinv == 0.0f && info == 0) info = k + 1;
-    if (c.tid == 0) c.piv[k] = p;
-    // interchange rows k and p; the new row k, normalised, goes to the copy
-    for (int j = c.tid; j < n; j += NT) {
-      const float rk = a[k * ld + j], rp = a[p * ld + j];
-      if (p != k) a[p * ld + j] = rk;
-      pr[j] = (j == k ? 1.0f : rp) * pinv;
-    }
-    __syncthreads();
-    const int cn = k + 1;              // next pivot column
-    const int own = cn & 31;           // lane owning column cn in the loops below
-    float v = -1.0f;
-    int bi = n;
-    for (int i = c.warp; i < n; i += NW) {
-      if (i == k) {
-        for (int j = c.lane; j < n; j += 32) a[k * ld + j] = pr[j];
-        continue;
-      }
-      const float fct = a[i * ld + k];
-      __syncwarp();
-      for (int j = c.lane; j < n; j += 32) {
-        const float nv = (j == k ? 0.0f : a[i * ld + j]) - fct * pr[j];
-        a[i * ld + j] = nv;
-        if (j == cn && i > k) {
-          const float x = fabsf(nv);
-          if (x > v || (x == v && i < bi)) { v = x; bi = i; }
-        }
-      }
-    }
-    (void)own;
-    warp_argmax_store(v, bi, c.lane, pmax, pidx, c.warp);
-    __syncthreads();
-  }
-  // column interchanges in reverse order; each thread owns whole rows
-  for (int i = c.tid; i < n; i += NT)
-    for (int k = n - 1; k >= 0; --k) {
-      const int p = c.piv[k];
-      if (p != k) {
-        const float t = a[i * ld + k];
-        a[i * ld + k] = a[i * ld + p];
-        a[i * ld + p] = t;
-      }
-    }
-  __syncthreads();
-  return info;
-}
-
-// Gauss-Jordan inverse (FP32) with the matrix in registers, by columns: warp w owns
-// the columns j = w + NW c (c < CC), lane l the rows l + 32 s (s < RS). Partial
-// pivoting by index (the unused row with the largest |a_ik|, lowest row index on
-// ties; rows are not moved, the k-th pivot row is recorded instead). The warp
-// owning column k searches it, publishes the pivot row p, 1/a_pk and the column (the multipliers) through
-// shared memory (double-buffered), and every warp then broadcasts the pivot row's
-// values of its own columns by warp shuffles and updates them: one CTA barrier per
-// column. Column k is first replaced by the unit vector e_p, so it ends up holding
-// column k of the inverse (in-place Gauss-Jordan). The inverse is written back as
-// inv[Pinv[i]][P[j]] = W[i][j] (P = pivot rows in step order). Requires n <= 32 RS
-// and n <= NW CC. Returns 0 or 1 + k for a zero pivot.
-template <int NW, int RS, int CC>
-__device__ int gj_invert_wc(Cta<NW>& c, float* A, int n) {
-  const int ld = odd_ld(n);
-  const int lane = c.lane, wp = c.warp;
-  float* pcol = reinterpret_cast<float*>(c.u);          // [2][n] multipliers (u: 6 n doubles)
-  int* pp = reinterpret_cast<int*>(c.red + SC_PIV);     // [2] pivot rows
-  float* pinvb = reinterpret_cast<float*>(pp + 2);      // [2] pivot reciprocals
-  float a[RS][CC];
-#pragma unroll
-  for (int s = 0; s < RS; ++s)
-#pragma unroll
-    for (int cc = 0; cc < CC; ++cc) {
-      const int i = lane + 32 * s, j = wp + NW * cc;
-      a[s][cc] = (i < n && j < n) ? A[i * ld + j] : 0.0f;
-    }
-  unsigned used = 0u;  // bit s: row lane + 32 s is a pivot row already
-  // owner warp of column k: search, then publish the pivot and the column
-  auto search = [&](int k, int buf) {
-    const int ck = k / NW;
-    float v[RS];
-#pragma unroll
-    for (int s = 0; s < RS; ++s) v[s] = 0.0f;
-#pragma unroll
-    for (int cc = 0; cc < CC; ++cc)
-      if (cc == ck) {
-#pragma unroll
-        for (int s = 0; s < RS; ++s) v[s] = a[s][cc];
-      }
-    // argmax of |a_ik| over the unused rows, lowest row on ties, NaN never chosen: the
-    // bit pattern of a non-negative float orders like its value, so key = bits + 1
-    // (0: no candidate) goes through one warp max-reduction; the first row slot, then
-    // the lowest lane, holding the maximum is the lowest row index that has it
-    unsigned key[RS];
-    unsigned kmax = 0u;
-#pragma unroll
-    for (int s = 0; s < RS; ++s) {
-      const int i = lane + 32 * s;
-      const float x = fabsf(v[s]);
-      key[s] = (i < n && !((used >> s) & 1u) && !isnan(x)) ? __float_as_uint(x) + 1u : 0u;
-      kmax = max(kmax, key[s]);
-    }
-    const unsigned km = __reduce_max_sync(FULLMASK, kmax);
-    int bi = n;
-    float bval = 0.0f;
-    if (km != 0u) {
-#pragma unroll
-      for (int s = 0; s < RS; ++s) {
-        const unsigned b = __ballot_sync(FULLMASK, key[s] == km);
-        if (bi == n && b != 0u) {
-          const int l = __ffs(b) - 1;
-          bi = l + 32 * s;
-          bval = __shfl_sync(FULLMASK, v[s], l);
-        }
-      }
-    }
-#pragma unroll
-    for (int s = 0; s < RS; ++s)
-      if (lane + 32 * s < n) pcol[buf * n + lane + 32 * s] = v[s];
-    if (lane == 0) {
-      const bool ok = bi < n && bval != 0.0f && isfinite(bval);
-      pp[buf] = bi < n ? bi : k;  // no candidate (NaN column): a safe index, zero pivot
-      pinvb[buf] = ok ? 1.0f / bval : 0.0f;
-    }
-  };
-  if (wp == 0) search(0, 0);
-  __syncthreads();
-  int info = 0;
-  for (int k = 0; k < n; ++k) {
-    const int buf = k & 1;
-    const int p = pp[buf];
-    const float pinv = pinvb[buf];
-    if (pinv == 0.0f && info == 0) info = k + 1;
-    if (c.tid == 0) c.piv[k] = p;
-    const int ps = p >> 5, pl = p & 31;
-    float f[RS];
-    bool isp[RS];
-#pragma unroll
-    for (int s = 0; s < RS; ++s) {
-      isp[s] = lane + 32 * s == p;
-      f[s] = lane + 32 * s < n ? pcol[buf * n + lane + 32 * s] : 0.0f;
-    }
-    // column k becomes e_p (it then receives column k of the inverse)
-    if (wp == k % NW) {
-      const int ck = k / NW;
-#pragma unroll
-      for (int cc = 0; cc < CC; ++cc)
-        if (cc == ck) {
-#pragma unroll
-          for (int s = 0; s < RS; ++s) a[s][cc] = isp[s] ? 1.0f : 0.0f;
-        }
-    }
-#pragma unroll
-    for (int cc = 0; cc < CC; ++cc) {
-      float src = a[0][cc];
-#pragma unroll
-      for (int s = 1; s < RS; ++s) src = ps == s ? a[s][cc] : src;
-      const float pr = __shfl_sync(FULLMASK, src, pl) * pinv;  // normalised pivot row
-#pragma unroll
-      for (int s = 0; s < RS; ++s) a[s][cc] = isp[s] ? pr : fmaf(-f[s], pr, a[s][cc]);
-    }
-#pragma unroll
-    for (int s = 0; s < RS; ++s)
-      if (isp[s]) used |= 1u << s;
-    const int k1 = k + 1;
-    if (k1 < n && wp == k1 % NW) search(k1, k1 & 1);
-    __syncthreads();
-  }
-  // inverse permutation of the pivot rows, then the scatter into the true inverse
-  for (int k = c.tid; k < n; k += NW * 32) c.perm[c.piv[k]] = k;
-  __syncthreads();
-#pragma unroll
-  for (int s = 0; s < RS; ++s)
-#pragma unroll
-    for (int cc = 0; cc < CC; ++cc) {
-      const int i = lane + 32 * s, j = wp + NW * cc;
-      if (i < n && j < n) A[c.perm[i] * ld + c.piv[j]] = a[s][cc];
-    }
-  __syncthreads();
-  return info;
-}
-
-// Solve M x = b for the FP64 right-hand side b; x written as double.
-// FP64: LU forward/back substitution. Otherwise: x = M32^-1 b with the FP32
-// inverse, then `ir` sweeps of r = b - M0 x (FP64, against the assembled matrix
-// M0) and x += M32^-1 r. One thread per row in every matrix-vector product.
-template <int NW, int PREC>
-__device__ void solve(Cta<NW>& c, int n, const double* b, double* x, int ir) {
-  constexpr int NT = NW * 32;
-  using P = Policy<PREC>;
-  if constexpr (!P::IR) {
-    for (int i = c.tid; i < n; i += NT) x[i] = b[c.perm[i]];
-    __syncthreads();
-    if (c.warp == Cta<NW>::SW) lu_solve_warp<double>(reinterpret_cast<double*>(c.M), n, c.invd, x, c.lane);
-    __syncthreads();
-  } else {
-    const float* Ai = reinterpret_cast<const float*>(c.M);
-    const typename P::ASM* M0 = reinterpret_cast<const typename P::ASM*>(c.M0);
-    float* xf = reinterpret_cast<float*>(c.sc);  // scratch vector reused as float
-    const int ld = odd_ld(n);
-    for (int i = c.tid; i < n; i += NT) xf[i] = (float)b[i];
-    __syncthreads();
-    for (int i = c.tid; i < n; i += NT) {
-      float acc = 0.0f;
-      const float* row = Ai + i * ld;
-      for (int j = 0; j < n; ++j) acc = fmaf(row[j], xf[j], acc);
-      x[i] = (double)acc;
-    }
-    __syncthreads();
-    for (int sweep = 0; sweep < ir; ++sweep) {
-      // FP64 residual rows from the last warp down (the first warps carry the species loops)
-      for (int i = NT - 1 - c.tid; i < n; i += NT) {
-        double acc = b[i];
-        const typename P::ASM* row = M0 + i * ld;
-        for (int j = 0; j < n; ++j) acc -= (double)row[j] * x[j];
-        xf[i] = (float)acc;
-      }
-      __syncthreads();
-      for (int i = c.tid; i < n; i += NT) {
-        float acc = 0.0f;
-        const float* row = Ai + i * ld;
-        for (int j = 0; j < n; ++j) acc = fmaf(row[j], xf[j], acc);
-        x[i] += (double)acc;
-      }
-      __syncthreads();
-    }
-  }
-}
-
-// Factorisation of the iteration matrix: LU (FP64 form) or the FP32 inverse.
-template <int NW, int PREC>
-__device__ int factor(Cta<NW>& c, int n, bool pivot = true) {
-  if constexpr (!Policy<PREC>::IR) {
-    return lu_factor<NW, double>(c, reinterpret_cast<double*>(c.M), n, pivot);
-  } else {
-    float* A = reinterpret_cast<float*>(c.M);
-    if constexpr (NW == 4) {
-      if (n <= 56) return gj_invert_wc<4, 2, 14>(c, A, n);
-      if (n <= 64) return gj_invert_wc<4, 2, 16>(c, A, n);
-    } else if constexpr (NW == 8) {
-      if (n <= 64) return gj_invert_wc<8, 2, 8>(c, A, n);
-      if (n <= 128) return gj_invert_wc<8, 4, 16>(c, A, n);
-    } else if constexpr (NW == 2) {
-      if (n <= 64) return gj_invert_wc<2, 2, 32>(c, A, n);
-    }
-    return gj_invert<NW>(c, A, n);
-  }
-}
-
-// Assemble the iteration matrix (fac = 1/(h gamma)) or the Jacobian (JO) in the
-// policy's assembly precision, then give the LU its own copy when they differ.
-template <int NW, int PREC, bool JO>
-__device__ void build_matrix(const DevMech& m, Cta<NW>& c, const Scal& s, const double* f, double fac) {
-  using P = Policy<PREC>;
-  if constexpr (!P::IR) {
-    assemble<NW, double, JO>(m, c, s, f, fac, c.M);
-  } else {
-    assemble<NW, typename P::ASM, JO>(m, c, s, f, fac, c.M0);
-    if (JO) return;
-    const int n = m.K + 1, ld = odd_ld(n);
-    const typename P::ASM* src = reinterpret_cast<const typename P::ASM*>(c.M0);
-    float* dst = reinterpret_cast<float*>(c.M);
-    for (int i = c.warp; i < n; i += NW)
-      for (int j = c.lane; j < n; j += 32) dst[i * ld + j] = (float)src[i * ld + j];
-    __syncthreads();
-  }
-}
-
-// Iteration matrix (FP64 form) from a forward-difference Jacobian, column by column:
-// J_.j = (f(y + d_j e_j) - f(y)) / d_j with d_j = sqrt(eps) max(|y_j|, floor_j)
-// (floor 1 K for T, 1e-6 for mass fractions: a smaller floor lets rounding in f
-// dominate the columns of trace species); S = sg J + fac I as in assemble.
-// Costs n RHS evaluations: the classical alternative to the analytical Jacobian.
-template <int NW, bool JO>
-__device__ void fd_matrix(const DevMech& m, Cta<NW>& c, double p, const double* y, const double* f0, double fac) {
-  constexpr int NT = NW * 32;
-  const int n = m.K + 1, ld = odd_ld(n);
-  double* A = reinterpret_cast<double*>(c.M);
-  for (int j = 0; j < n; ++j) {
-    const double d = 1.4901161193847656e-8 * fmax(fabs(y[j]), j == 0 ? 1.0 : 1e-6);
-    for (int i = c.tid; i < n; i += NT) c.ys[i] = y[i] + (i == j ? d : 0.0);
-    __syncthreads();
-    eval_rhs<NW, false, false>(m, c, c.ys, p, c.fv);
-    const double id = 1.0 / d;
-    for (int i = c.tid; i < n; i += NT) {
-      const double J = (c.fv[i] - f0[i]) * id;
-      A[i * ld + j] = JO ? J : -J + (i == j ? fac : 0.0);
-    }
-    __syncthreads();
-  }
-}
-
-// WRMS norm of e with scale atol + rtol max(|ya|, |yb|). With step_fac, also the
-// step-size factor 0.9 err^(-1/q) (q = 4: RODAS4, 3: ROS34PW2; kFacMax for err = 0);
-// both come from the CTA's last warp.
-template <int NW>
-__device__ double wrms(Cta<NW>& c, int n, const double* e, const double* ya, const double* yb,
-                       double rtol, double atol, double* step_fac = nullptr, int q = 4) {
-  constexpr int NT = NW * 32;
-  double part[1] = {0.0};
-  for (int i = c.tid; i < n; i += NT) {
-    const double sc = atol + rtol * fmax(fabs(ya[i]), fabs(yb[i]));
-    const double r = e[i] / sc;
-    part[0] += r * r;
-  }
-  double o[2];
-  c.reduce(part, warps_for<NW>(n), [&](const double (&t)[1], double (&r)[2]) {
-    const double err = sqrt(t[0] / n);
-    r[0] = err;
-    r[1] = err > 0.0 ? kSafety / (q == 4 ? sqrt(sqrt(err)) : cbrt(err)) : kFacMax;
-  }, o);
-  if (step_fac) *step_fac = o[1];
-  return o[0];
-}
-
-// Hairer-Wanner starting step (Solving ODEs I, Sec. II.4) in the WRMS norm with
-// scale atol + rtol |y0|, exponent 1/q (the method's embedded order + 1), clamped
-// to dt; a vanishing derivative selects the whole interval. Uses f0 = f(y0)
-// (already in c.f0) and c.ys, c.fv.
-template <int NW, bool FF = false>
-__device__ double starting_step(const DevMech& m, Cta<NW>& c, double p, double dt, double rtol,
-                                double atol, int q = 4) {
-  constexpr int NT = NW * 32;
-  const int n = m.K + 1;
-  const double d0 = wrms(c, n, c.y, c.y, c.y, rtol, atol);
-  const double d1 = wrms(c, n, c.f0, c.y, c.y, rtol, atol);
-  double ha = (d1 > 1e-300) ? 0.01 * d0 / d1 : dt;
-  ha = fmin(ha, dt);
-  for (int i = c.tid; i < n; i += NT) c.ys[i] = c.y[i] + ha * c.f0[i];
-  __syncthreads();
-  eval_rhs<NW, false, FF>(m, c, c.ys, p, c.fv);
-  for (int i = c.tid; i < n; i += NT) c.rr[i] = c.fv[i] - c.f0[i];
-  __syncthreads();
-  const double d2 = wrms(c, n, c.rr, c.y, c.y, rtol, atol) / ha;
-  const double mx = fmax(d1, d2);
-  const double hb = (mx > 1e-300) ? (q == 4 ? pow(0.01 / mx, 0.25) : cbrt(0.01 / mx)) : dt;
-  return fmin(fmin(100.0 * ha, hb), dt);
-}
-
-// Mass enthalpy and heat capacity at T for mass fractions Y (CTA sums).
-template <int NW>
-__device__ void h_cp_mass(const DevMech& m, Cta<NW>& c, double T, const double* Y, double& h,
-                          double& cp) {
-  constexpr int NT = NW * 32;
-  const double invT = 1.0 / T;
-  double part[2] = {0.0, 0.0};
-  for (int k = c.tid; k < m.K; k += NT) {
-    const double* a = m.nasa + 36 * k;
-    a += (T < a[34]) ? 0 : 17;
-    const double cpr = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
-    const double hr = a[5] + T * (a[6] + T * (a[7] + T * (a[8] + T * a[9]))) + a[10] * invT;
-    part[0] += Y[k] * hr * m.invW[k];
-    part[1] += Y[k] * cpr * m.invW[k];
-  }
-  c.sum(part, warps_for<NW>(m.K));
-  h = part[0] * kRc * T;
-  cp = part[1] * kRc;
-}
-
-// ---------------------------------------------------------------------------
-// one cell
-// ---------------------------------------------------------------------------
-// Per-phase cycle counters (diagnostic; thread 0 reads the clock right after the
-// CTA barriers that close each phase): 0 load + starting step, 1 RHS and Jacobian
-// data at the step point, 2 iteration-matrix assembly, 3 factorisation, 4 stage RHS,
-// 5 stage solves, 6 stage combination + error norm + control, 7 T recovery + store.
-#define PHASE(k)                                                              \
-  do {                                                                        \
-    if (prof) {                                                               \
-      const long long now_ = clock64();                                       \
-      atomicAdd(args.phase + cur_, (unsigned long long)(now_ - last_));       \
-      last_ = now_;                                                           \
-      cur_ = (k);                                                             \
-    }                                                                         \
-  } while (0)
-
-template <int NW, int PREC>
-__device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs& args, Cta<NW>& c) {
-  const bool prof = args.phase != nullptr && c.tid == 0;
-  long long last_ = prof ? clock64() : 0;
-  int cur_ = 0;
-  constexpr int NT = NW * 32;
-  const DevMech& m = job.m;
-  const int K = m.K, n = K + 1;
-  const double p = job.p[cell];
-  const double dt = args.dt, rtol = args.rtol, atol = args.atol;
-  // load (coalesced over species)
-  if (c.tid == 0) c.y[0] = job.T[cell];
-  for (int k = c.tid; k < K; k += NT) c.y[1 + k] = job.Y[(size_t)cell * K + k];
-  __syncthreads();
-  int status = CHEM_CELL_OK;
-  {
-    double part[1] = {0.0};
-    for (int i = c.tid; i < n; i += NT) part[0] += isfinite(c.y[i]) ? 0.0 : 1.0;
-    c.sum(part, warps_for<NW>(n));
-    if (part[0] > 0.0 || !(c.y[0] > 0.0) || !(p > 0.0)) status = CHEM_CELL_NONFINITE;
-  }
-  int steps = 0, rejects = 0;
-  double h_first = 0.0, h_next = 0.0;
-  if (status == CHEM_CELL_OK) {
-    double h_target, cp_dummy;
-    h_cp_mass(m, c, c.y[0], c.y + 1, h_target, cp_dummy);
-    // initial step
-    double h = -1.0;
-    bool guard = false;  // a supplied initial step, checked against f(y0) at the first step
-    if (args.use_h0 && job.h0) {
-      const double g = job.h0[cell];
-      if (isfinite(g) && g > 0.0) {
-        h = fmin(g, dt);
-        guard = true;
-      }
-    }
-    if (h <= 0.0) {
-      eval_rhs<NW, false, Policy<PREC>::IR>(m, c, c.y, p, c.f0);
-      h = starting_step<NW, Policy<PREC>::IR>(m, c, p, dt, rtol, atol, args.tab.q);
-    }
-    double t = 0.0, h_unclipped = h;
-    bool after_reject = false;
-    while (true) {
-      if (dt - t <= 1e-12 * dt) break;
-      if (steps >= args.max_steps) { status = CHEM_CELL_MAX_STEPS; break; }
-      if (!(h >= kHmin)) { status = CHEM_CELL_H_UNDERFLOW; break; }  // also catches NaN
-      h_unclipped = h;
-      if (t + h > dt) h = dt - t;
-      ++steps;
-      // Jacobian and f0 at y; iteration matrix; factorisation
-      PHASE(1);
-      // A supplied initial step (learned or carried over) is kept inside the starting
-      // step heuristic's envelope [h_a, 100 h_a], h_a = 0.01 |y0| / |f(y0)| in the WRMS
-      // norm: f(y0) is the first step's first-stage RHS, so the check costs no RHS
-      // evaluation, and a prediction far from the states it was trained on cannot cost
-      // more than the heuristic's own range of answers.
-      auto apply_guard = [&]() {
-        if (!guard) return;
-        guard = false;
-        const double d0 = wrms(c, n, c.y, c.y, c.y, rtol, atol);
-        const double d1 = wrms(c, n, c.f0, c.y, c.y, rtol, atol);
-        const double ha = d1 > 1e-300 ? 0.01 * d0 / d1 : dt;
-        h = fmin(fmin(fmax(h, ha), 100.0 * ha), dt - t);
-        h_unclipped = h;
-      };
-      if (PREC == PREC_FP64 && args.jac_fd) {
-        eval_rhs<NW, false, false>(m, c, c.y, p, c.f0);
-        apply_guard();
-        PHASE(2);
-        fd_matrix<NW, false>(m, c, p, c.y, c.f0, 1.0 / (h * args.tab.gamma));
-      } else {
-        const Scal s = eval_rhs<NW, true, Policy<PREC>::IR>(m, c, c.y, p, c.f0);
-        apply_guard();
-        PHASE(2);
-        build_matrix<NW, PREC, false>(m, c, s, c.f0, 1.0 / (h * args.tab.gamma));
-      }
-      PHASE(3);
-      const int info = factor<NW, PREC>(c, n, !(PREC == PREC_FP64 && args.no_pivot));
-      PHASE(6);
-      double err, step_fac = kFacMin;
-      if (info != 0) {
-        err = NAN;
-      } else {
-        const double invh = 1.0 / h;
-        const MethodTab& tb = args.tab;
-        const int S = tb.s;
-#pragma unroll 1
-        for (int st = 0; st < S; ++st) {
-          const double* fs = c.f0;
-          if (st > 0) {
-            PHASE(6);
-            for (int i = c.tid; i < n; i += NT) {
-              double v = c.y[i];
-              for (int j = 0; j < st; ++j) v += tb.a[st][j] * c.u[j * n + i];
-              c.ys[i] = v;
-            }
-            __syncthreads();
-            PHASE(4);
-            eval_rhs<NW, false, Policy<PREC>::IR>(m, c, c.ys, p, c.fv);
-            fs = c.fv;
-          }
-          PHASE(6);
-          // stage right-hand side f(y_s) + sum_j (c_sj / h) u_j, in place in fv
-          for (int i = c.tid; i < n; i += NT) {
-            double v = 0.0;
-            for (int j = 0; j < st; ++j) v += tb.c[st][j] * c.u[j * n + i];
-            c.fv[i] = fma(invh, v, fs[i]);
-          }
-          __syncthreads();
-          PHASE(5);
-          solve<NW, PREC>(c, n, c.fv, c.u + st * n, args.ir_sweeps);
-        }
-        PHASE(6);
-        for (int i = c.tid; i < n; i += NT) {
-          double v = c.y[i], e = 0.0;
-          for (int j = 0; j < S; ++j) {
-            v += tb.m[j] * c.u[j * n + i];
-            if (!tb.e_last) e += tb.e[j] * c.u[j * n + i];
-          }
-          c.yn[i] = v;
-          if (!tb.e_last) c.rr[i] = e;
-        }
-        __syncthreads();
-        err = wrms(c, n, tb.e_last ? c.u + (S - 1) * n : c.rr, c.y, c.yn, rtol, atol, &step_fac, tb.q);
-      }
-      if (!(err <= 1.0)) {
-        ++rejects;
-        after_reject = true;
-        h *= isfinite(err) ? fmax(step_fac, kFacMin) : kFacMin;
-        continue;
-      }
-      t += h;
-      for (int i = c.tid; i < n; i += NT) c.y[i] = c.yn[i];
-      __syncthreads();
-      if (h_first == 0.0) h_first = h;
-      const double fac = fmin(fmax(step_fac, kFacMin), after_reject ? 1.0 : kFacMax);
-      after_reject = false;
-      h *= fac;
-    }
-    // step size to carry to the next call: the controller's proposal, or the step
-    // before the final clipping to dt when that was longer
-    h_next = fmax(h, h_unclipped);
-    // temperature from the conserved mass enthalpy (Newton, |dT| < 1e-10 T)
-    PHASE(7);
-    if (status == CHEM_CELL_OK) {
-      double T = c.y[0];
-      for (int it = 0; it < 50; ++it) {
-        double hm, cpm;
-        h_cp_mass(m, c, T, c.y + 1, hm, cpm);
-        const double dT = (hm - h_target) / cpm;
-        T -= dT;
-        if (fabs(dT) < 1e-10 * T) break;
-      }
-      if (!(T >= kTmin && T <= kTmax)) status = CHEM_CELL_T_RANGE;
-      else if (c.tid == 0) c.y[0] = T;
-      __syncthreads();
-    }
-  }
-  // store (the last accepted state for failed cells)
-  if (status != CHEM_CELL_NONFINITE) {
-    if (c.tid == 0) job.T[cell] = c.y[0];
-    for (int k = c.tid; k < K; k += NT) job.Y[(size_t)cell * K + k] = c.y[1 + k];
-  }
-  PHASE(7);
-  if (c.tid == 0) {
-    if (job.st.substeps) job.st.substeps[cell] = steps;
-    if (job.st.rejects) job.st.rejects[cell] = rejects;
-    if (job.st.h_first) job.st.h_first[cell] = h_first;
-    if (job.st.status) job.st.status[cell] = status;
-    if (job.st.h_last) job.st.h_last[cell] = status == CHEM_CELL_OK ? h_next : 0.0;
-    if (job.cost_out) job.cost_out[cell] = (float)steps;
-  }
-  __syncthreads();
-}
-
-// ---------------------------------------------------------------------------
-// kernels
-// ---------------------------------------------------------------------------
-// Launch bounds: 128 registers a thread for four CTAs of 128 threads (FP64 form: its
-// shared-memory footprint allows no more up to ~60 species), eight of 64 or two of 256;
-// the mixed form with 128 threads takes 96 registers for five CTAs per SM, which its
-// global-memory matrix slot makes room for (measured on 54 species: 7 % faster than
-// four CTAs; six and seven CTAs spill too much in the register Gauss-Jordan).
-template <int NW, int PREC>
-__global__ void __launch_bounds__(NW * 32, NW == 4 ? (PREC == PREC_MIXED ? 5 : 4) : NW == 2 ? 8 : 2) k_integrate(const __grid_constant__ IntegrateArgs args) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ long long s_work;
-  const bool m0g = PREC == PREC_MIXED && args.m0_scratch != nullptr;
-  const Layout L = make_layout(args.smem_K, args.smem_I, PREC, m0g);
-  Cta<NW> c;
-  c.bind(smem, L);
-  if (m0g) c.M0 = args.m0_scratch + (size_t)blockIdx.x * args.m0_stride;
-  c.load_tables();  // first read after the barrier that ends each cell's state load
-  for (long long it = 0;; ++it) {
-    long long w;
-    if (args.sched == SCHED_PLAIN) {
-      if (it > 0) break;
-      w = blockIdx.x;
-    } else if (args.sched == SCHED_STATIC) {
-      w = blockIdx.x + it * (long long)gridDim.x;
-    } else {
-      if (threadIdx.x == 0) s_work = atomicAdd(args.queue, 1);
-      __syncthreads();
-      w = s_work;
-      __syncthreads();
-    }
-    if (w >= args.n_total) break;
-    const long long g = args.perm ? args.perm[w] : w;
-    int j = 0;
-    while (j + 1 < args.n_jobs && g >= args.jobs[j + 1].offset) ++j;
-    integrate_cell<NW, PREC>(args.jobs[j], g - args.jobs[j].offset, args, c);
-  }
-}
+// W-method instantiations (chem_kernels_w.cu)
+cudaError_t launch_integrate_w(const IntegrateArgs& a, int block, int prec, int grid, cudaStream_t st);
 
 struct DiagArgs {
   DevMech m;
@@ -1777,21 +109,13 @@ __global__ void __launch_bounds__(NW * 32) k_lu_solve(const __grid_constant__ Lu
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
-template <class KernelT>
-static cudaError_t prep(KernelT k, size_t smem) {
-  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-
 template <int NW, int PREC>
 static cudaError_t launch_integrate_t(const IntegrateArgs& a, int grid, cudaStream_t st) {
-  const size_t smem = smem_bytes(a.smem_K, a.smem_I, PREC, a.m0_scratch != nullptr);
-  cudaError_t e = prep(k_integrate<NW, PREC>, smem);
-  if (e != cudaSuccess) return e;
-  k_integrate<NW, PREC><<<grid, NW * 32, smem, st>>>(a);
-  return cudaGetLastError();
+  return launch_integrate_m<NW, PREC, METHOD_RODAS4>(a, grid, st);
 }
 
 cudaError_t launch_integrate(const IntegrateArgs& a, int block, int prec, int grid, cudaStream_t st) {
+  if (a.tab.s == 4) return launch_integrate_w(a, block, prec, grid, st);
 #define LI(P)                                                                       \
   do {                                                                              \
     if (block == 64) return launch_integrate_t<2, P>(a, grid, st);                  \
@@ -1807,12 +131,12 @@ cudaError_t launch_integrate(const IntegrateArgs& a, int block, int prec, int gr
 cudaError_t occupancy_integrate(int block, int prec, int K, int I, int* ctas_per_sm, bool m0_global) {
   const size_t smem = smem_bytes(K, I, prec, m0_global);
   cudaError_t e;
-#define OCC(NW, P)                                                                         \
-  do {                                                                                     \
-    e = prep(k_integrate<NW, P>, smem);                                                    \
-    if (e != cudaSuccess) return e;                                                        \
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_integrate<NW, P>, \
-                                                         NW * 32, smem);                   \
+#define OCC(NW, P)                                                                                    \
+  do {                                                                                                \
+    e = prep(k_integrate<NW, P, METHOD_RODAS4>, smem);                                                \
+    if (e != cudaSuccess) return e;                                                                   \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_integrate<NW, P, METHOD_RODAS4>, \
+                                                         NW * 32, smem);                              \
   } while (0)
 #define OCCP(P)                  \
   do {                           \
