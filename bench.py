@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--retrain-every", type=int, default=0,
                     help="with --cfd-loop: retrain the model every N steps on the learned form's own logs "
                          "of the last N steps (0: train once, on steps 1-5)")
+    ap.add_argument("--no-h0-guard", action="store_true",
+                    help="with --cfd-loop: the learned initial step as predicted, without the starting-step "
+                         "envelope check (option h0_guard = 0)")
     ap.add_argument("--no-learned-order", action="store_true",
                     help="with --cfd-loop: learned initial step only, index order")
     ap.add_argument("--refmap", action="store_true",
@@ -86,6 +89,10 @@ def parse():
                     help="the batching configuration, FP64 throughout: 262,144 cells of the 54-species "
                          "workload, plain launch vs work queue + autotuner + CUDA graph; then four "
                          "mechanisms (10, 32, 54, 100 species) in one launch vs four launches")
+    ap.add_argument("--precision-forms", action="store_true",
+                    help="the precision configuration: 100 species, 262,144 cells at 40 bar (c100_262k unless "
+                         "--workload names another): plain FP64, mixed with 1, 2 and 3 refinement sweeps, and the "
+                         "W-method with FP32 assembly; sampled same-run parity; one JSON line each")
     ap.add_argument("--no-phases", action="store_true",
                     help="skip the extra untimed step per form with per-phase cycle counters")
     ap.add_argument("--parity-per-class", type=int, default=512,
@@ -628,6 +635,60 @@ def run_batching(args):
                           "block": int(integs[0].get_option("last_block")), "substeps": sub}), flush=True)
 
 
+def run_precision_forms(args):
+    """The precision configuration: each form integrates the same 262,144-cell batch of
+    the 100-species workload (one warm-up call, two timed calls from the same input,
+    CUDA events on the stream, median); per form the Rosenbrock steps, rejections and
+    the per-result error against the FP64 oracle on a stratified sample (the same
+    cells for every form)."""
+    import torch
+
+    import paper_2112_05834_gb300 as pkg
+
+    wl = "c100_262k" if args.workload == "c54_65k" else args.workload
+    m, st, dt = synth.workload(wl, n_cells=args.cells)
+    n = st.T.shape[0]
+    dev = torch.device("cuda", 0)
+    T0, p, Y0 = (torch.tensor(a, device=dev) for a in (st.T, st.p, st.Y))
+    stream = torch.cuda.current_stream()
+    forms = [("plain_fp64", dict(precision=0, scheduler=0)),
+             ("mixed_ir1", dict(precision=1, scheduler=2, ir_sweeps=1)),
+             ("mixed_ir2", dict(precision=1, scheduler=2, ir_sweeps=2)),
+             ("mixed_ir3", dict(precision=1, scheduler=2, ir_sweeps=3)),
+             ("w_method_fp32_assembly", dict(precision=2, scheduler=2, ir_sweeps=1, method=1))]
+    res = {}
+    for name, opt in forms:
+        integ = pkg.Integrator(m, **opt)
+        times = []
+        for rep in range(3):
+            T, Y = T0.clone(), Y0.clone()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            integ.integrate(T, p, Y, dt, RTOL, ATOL)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep > 0:
+                times.append(e0.elapsed_time(e1))
+        tot = integ.totals()
+        res[name] = {"T": T.cpu().numpy(), "Y": Y.cpu().numpy(), "ms": float(np.median(times)),
+                     "cell_substeps": integ.stats(n)["substeps"].cpu().numpy(), "tot": tot,
+                     "block": int(integ.get_option("last_block"))}
+        integ.close()
+    par = same_run_parity(m, st, dt, {k: v for k, v in res.items()}, args.parity_per_class // 8,
+                          args.parity_costliest // 8)
+    base = res["plain_fp64"]["ms"]
+    for name, _ in forms:
+        r = res[name]
+        print(json.dumps({"precision_form": name, "workload": wl, "n_cells": n, "rtol": RTOL, "atol": ATOL,
+                          "cells_per_s": n / (r["ms"] * 1e-3), "call_ms": r["ms"], "speedup_vs_plain_fp64": base / r["ms"],
+                          "substeps": r["tot"]["substeps"], "rejects": r["tot"]["rejects"],
+                          "failed": r["tot"]["failed"], "block": r["block"], "parity": par["forms"][name],
+                          "parity_cells": par["cells"]}), flush=True)
+    if not par["ok"]:
+        sys.exit(1)
+
+
 def run_cfd_loop(args):
     """Learned scheduling + initial step at scale: the 100-species mechanism, 1,048,576
     cells (or --cells), 20 CFD steps of dt with the seeded mixing perturbation between
@@ -673,6 +734,7 @@ def run_cfd_loop(args):
             model.attach(learned)
             learned.set_option("order", 0 if args.no_learned_order else 1)
             learned.set_option("h0", 1)
+            learned.set_option("h0_guard", 0 if args.no_h0_guard else 1)
             logs.clear()
         if args.retrain_every and step > 6 and (step - 6) % args.retrain_every == 0 and logs:
             t0 = time.perf_counter()
@@ -703,7 +765,7 @@ def run_cfd_loop(args):
         st = synth.perturb_states(synth.CellStates(T=T.cpu().numpy(), p=st.p, Y=Y.cpu().numpy(), kind=st.kind),
                                   seed=100 + step)
     print(json.dumps({"cfd_loop_summary": "steps 6-20", "n_cells": n, "retrain_every": args.retrain_every,
-                      "learned_order": not args.no_learned_order,
+                      "learned_order": not args.no_learned_order, "h0_guard": not args.no_h0_guard,
                       "plain_cells_step_per_s": 15 * n / (tot["plain_ms"] / 1e3),
                       "learned_cells_step_per_s": 15 * n / (tot["learned_ms"] / 1e3),
                       "speedup": tot["plain_ms"] / tot["learned_ms"],
@@ -765,6 +827,9 @@ def main():
         return
     if args.batching:
         run_batching(args)
+        return
+    if args.precision_forms:
+        run_precision_forms(args)
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

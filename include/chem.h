@@ -212,6 +212,10 @@ chem_status chem_integrate_jobs(const chem_job* jobs, int32_t n_jobs, double dt,
  *                 2 = carried over: each cell starts from the step size the
  *                 controller proposed after its last step in the handle's
  *                 previous call of the same size (the heuristic otherwise)
+ *   "h0_guard"    1 (default) = a supplied initial step (learned or carried over)
+ *                 is kept, at the cell's first step, inside the starting-step
+ *                 heuristic's envelope [h_a, 100 h_a], h_a = 0.01 |y0| / |f(y0)| in
+ *                 the WRMS norm (no extra RHS evaluation); 0 = taken as supplied
  *   "max_steps"   step budget per cell (default 100000)
  *   "block"       threads per cell: 64, 128 or 256; 0 (default) = the size with
  *                 the most resident warps per SM for the mechanism and precision

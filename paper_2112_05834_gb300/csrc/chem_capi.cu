@@ -639,6 +639,7 @@ static const OptionDef kOptions[] = {
     {"pivoting", &chem_handle_s::pivoting, 0, 1},
     {"job_launch", &chem_handle_s::job_launch, 0, 1},
     {"method", &chem_handle_s::method, 0, 1},
+    {"h0_guard", &chem_handle_s::h0_guard, 0, 1},
 };
 
 extern "C" chem_status chem_set_option(chem_handle h, const char* key, double value) {
@@ -754,6 +755,7 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
   a.perm = nullptr;
   a.phase = nullptr;
   a.tab = method_tableau(h0->method);
+  a.h0_guard = h0->h0_guard;
   if (h0->profile) {
     if (!h0->d_phase) {
       chem_status ps = chem_internal_alloc(h0, &h0->d_phase, 8 * sizeof(unsigned long long));

@@ -44,6 +44,7 @@ struct chem_handle_s {
   int pivoting = 1;                       // option "pivoting": 0 = no row interchanges (FP64 form)
   int job_launch = 0;                     // option "job_launch": 1 = one launch per job, concurrent streams
   int method = 0;                         // option "method": 0 = RODAS4, 1 = ROS34PW2 (W-method)
+  int h0_guard = 1;                       // option "h0_guard": envelope check of supplied initial steps
   cudaStream_t side = nullptr;            // the handle's stream for concurrent jobs
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t kev0 = nullptr, kev1 = nullptr;

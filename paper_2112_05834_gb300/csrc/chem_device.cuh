@@ -1532,7 +1532,7 @@ __device__ void integrate_cell(const Job& job, int64_t cell, const IntegrateArgs
       const double g = job.h0[cell];
       if (isfinite(g) && g > 0.0) {
         h = fmin(g, dt);
-        guard = true;
+        guard = args.h0_guard != 0;
       }
     }
     if (h <= 0.0) {

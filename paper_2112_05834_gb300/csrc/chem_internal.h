@@ -115,6 +115,7 @@ struct IntegrateArgs {
   int sched;
   int ir_sweeps;
   int use_h0;          // 1: take jobs[j].h0 when finite and positive
+  int h0_guard;        // 1: keep a supplied initial step inside the starting-step envelope
   int jac_fd;          // FP64 form only: 1 = forward-difference Jacobian (n extra RHS evaluations)
   int no_pivot;        // FP64 form only: 1 = Gaussian elimination without row interchanges
   int smem_K, smem_I;  // sizes the shared-memory carve-up was computed for
