@@ -224,6 +224,30 @@ struct Pool {
 
 }  // namespace
 
+// The temperature below which some species may have |G/RT| > kBigGRT, from G/RT of
+// every species on a 0.25 K grid over [kTmin, kTmax] with a threshold 10 below
+// kBigGRT: by d(G/RT)/dT = -(H/RT)/T, |G/RT| changes by at most 0.25 |H/RT| / T
+// between grid points, under 10 while |H/RT| < 40 T (8,000 at 200 K). A mechanism
+// with a larger |H/RT| anywhere in the range always takes the one-exponential path.
+// Returns 0 when no species comes near the threshold in the whole range.
+static double big_gibbs_temperature(const chem_mechanism_desc* d) {
+  const double thr = kBigGRT - 10.0;
+  double Tb = 0.0;
+  for (int k = 0; k < d->n_species; ++k) {
+    bool found = false;
+    for (double T = kTmax; T >= kTmin; T -= 0.25) {
+      const double* a = (T < d->T_mid[k] ? d->nasa_lo : d->nasa_hi) + 7 * k;
+      const double hrt = h_RT(a, T);
+      if (!(std::fabs(hrt) < 40.0 * T)) return 1e300;
+      if (!found && std::fabs(hrt - s_R(a, T)) > thr) {
+        Tb = std::max(Tb, T + 0.25);
+        found = true;
+      }
+    }
+  }
+  return Tb;
+}
+
 static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
   const int K = d->n_species, I = d->n_reactions;
   // sort reactions by kind so each warp meets at most a few kinds
@@ -485,6 +509,7 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
   m.i_tb0 = i_tb0;
   m.i_fo0 = i_fo0;
   m.i_troe0 = i_troe0;
+  m.T_bigG = big_gibbs_temperature(d);
   m.W = reinterpret_cast<const double*>(b + oW);
   m.invW = reinterpret_cast<const double*>(b + oiW);
   m.nasa = reinterpret_cast<const double*>(b + oN);

@@ -120,9 +120,6 @@ static __device__ const double2 g_exp2_tab[32] = {
 static __device__ __noinline__ double exp_outside(double x) { return exp(x); }
 
 constexpr double kInvLn10 = 0.43429448190325176;  // 1 / ln 10
-// Largest |G/RT| of a species for which the reverse-rate ratio is formed as a
-// product of per-species factors exp(+-G/RT): four factors stay within e^+-600.
-constexpr double kBigGRT = 150.0;
 constexpr double kLnRcP0 = 4.407418589020958;  // ln(Rc / P0), cgs
 
 __device__ __forceinline__ double xexp(double x, const double2* tab) {
@@ -588,7 +585,6 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
     if (c.lane == 0) {
       c.red[SC_LOGT] = lg;
       c.red[SC_INVT] = invT0;
-      c.red[SC_FLAG] = 0.0;  // set below when some |G/RT| is too large for the factor products
     }
   }
   {
@@ -609,6 +605,11 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
   s.logT = c.red[SC_LOGT];
   s.invT = c.red[SC_INVT];
   const double T = s.T, invT = s.invT, logT = s.logT;
+  // Below m.T_bigG some species may have |G/RT| > kBigGRT (very low T with large
+  // formation enthalpies): there the reverse-rate ratio takes one exponential of the
+  // summed exponent per reaction instead of the product of four species factors,
+  // whose partial products could overflow or underflow.
+  const bool bigG = T < m.T_bigG;
   // species: thermo, exp(G/RT), concentrations
   for (int k = c.tid; k < K; k += NT) {
     const double* a = m.nasa + 36 * k;
@@ -622,8 +623,7 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
     const double e = xexp(g, c.etab);
     c.eg[k] = e;
     c.ieg[k] = xrcp(e);
-    c.ek[k] = g;  // G/RT (the slot is the Jacobian assembly's, unused until then)
-    if (fabs(g) > kBigGRT) c.red[SC_FLAG] = 1.0;
+    if (bigG) c.ek[k] = g;  // G/RT (the slot is the Jacobian assembly's, unused until then)
     const double Ck = s.rho * y[1 + k] * m.invW[k];
     c.C[k] = Ck;
     // float-float copy of C for the third-body sums (the slot of d_k, which the
@@ -634,10 +634,6 @@ __device__ Scal eval_rhs(const DevMech& m, Cta<NW>& c, const double* y, double p
   __syncthreads();
   const double cRT = kRc * T / kP0;  // (P0 / (Rc T))^-1
   const double icRT = kP0 * invT / kRc;
-  // A cell with some |G/RT| > kBigGRT (very low T with large formation enthalpies)
-  // takes one exponential of the summed exponent per reaction instead of the product
-  // of four species factors, whose partial products could overflow or underflow.
-  const bool bigG = c.red[SC_FLAG] != 0.0;
   // 32-reaction chunks of one kind each, dealt to the warps by estimated work
   const int* cs = m.chunk_sched[NW == 2 ? 0 : NW == 4 ? 1 : 2];
   for (int pos = cs[c.warp]; pos < cs[c.warp + 1]; ++pos) {

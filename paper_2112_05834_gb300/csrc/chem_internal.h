@@ -13,6 +13,9 @@ constexpr int kMaxJobs = 8;
 constexpr double kRc = 8.31446261815324e7;  // erg / (mol K)
 constexpr double kP0 = 1.01325e6;           // dyn / cm^2, standard state (1 atm)
 constexpr double kTmin = 200.0, kTmax = 6000.0;
+// Largest |G/RT| of a species for which the reverse-rate ratio is formed as a product
+// of per-species factors exp(+-G/RT): four factors then stay within e^+-600.
+constexpr double kBigGRT = 150.0;
 
 // FP64: everything in FP64.
 // MIXED: Jacobian assembled in FP64 (kept for the refinement residual), LU and
@@ -53,6 +56,7 @@ struct DevMech {
   int i_tb0;  // first reaction of kind >= 1 (sorted order)
   int i_fo0;  // first reaction of kind >= 2
   int i_troe0;  // first reaction of kind 3
+  double T_bigG;  // below this T some species may have |G/RT| > kBigGRT (0: never in [kTmin, kTmax])
   const double* W;      // [K]
   const double* invW;   // [K]
   const double* nasa;   // [K][36]: for range r (0 below T_mid, 1 above) at 17 r:
