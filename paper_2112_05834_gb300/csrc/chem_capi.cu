@@ -288,25 +288,27 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
       if (d->rxn_type[order[i]] == kind) padded.push_back(order[i]);
     if (padded.size() == first) continue;
     while (padded.size() % 32) padded.push_back(-1);
-    // relative latency of one chunk in the reaction phase (per-warp timings of the
-    // 54-species mechanism: third-body chunks add the float-float [M] sums; the
-    // falloff kinds keep only their concentration-dependent part, the rest is done
-    // in the species phase)
-    const double cost = kind == 0 ? 28.0 : kind == 1 ? 41.0 : kind == 2 ? 46.0 : 82.0;
+    const double cost = kind == 0 ? 28.0 : kind == 1 ? 31.0 : kind == 2 ? 60.0 : 220.0;
     for (size_t c = first; c < padded.size(); c += 32) chunk_cost.push_back(cost);
   }
   const int Ip = (int)padded.size();
   const int n_chunks = (int)chunk_cost.size();
   // Deal the chunks to warps, longest first, each to the warp with the least estimated
-  // work so far. The reaction phase is bounded by barriers on both sides (the species
-  // phase before it, the production sums after), so only its own work is balanced.
+  // work so far; the species loops (thermo, production rates: ~72 per 32 species) load
+  // the warps holding species and the CTA's scalar work (~60) the last warp.
   std::vector<int> by_cost(n_chunks);
   std::iota(by_cost.begin(), by_cost.end(), 0);
   std::stable_sort(by_cost.begin(), by_cost.end(), [&](int a, int b) { return chunk_cost[a] > chunk_cost[b]; });
   std::vector<int> chunk_sched[3];
   for (int v = 0; v < 3; ++v) {
-    const int NW = 2 << v;
+    const int NW = 2 << v, NT = 32 * NW;
     std::vector<double> load(NW, 0.0);
+    for (int w = 0; w < NW; ++w) {
+      int cnt = 0;
+      for (int k = 0; k < K; ++k) cnt += (k % NT) / 32 == w;
+      load[w] = 72.0 * ((cnt + 31) / 32);
+    }
+    load[NW - 1] += 60.0;
     std::vector<std::vector<int>> own(NW);
     for (int ch : by_cost) {
       int w = 0;
@@ -727,7 +729,7 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
   IntegrateArgs a;
   std::memset(&a, 0, sizeof a);
   int64_t total = 0;
-  int Kmax = 0, Imax = 0, Fmax = 0;
+  int Kmax = 0, Imax = 0;
   for (int j = 0; j < n_jobs; ++j) {
     chem_handle h = jobs[j].h;
     chem_status s = ensure_stats(h, jobs[j].n_cells);
@@ -756,7 +758,6 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
     total += jobs[j].n_cells;
     Kmax = std::max(Kmax, h->K);
     Imax = std::max(Imax, h->I);
-    Fmax = std::max(Fmax, h->dm.I - h->dm.i_troe0);
   }
   if (total == 0) return CHEM_OK;
   if (total > 2147483647LL) {
@@ -775,7 +776,6 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
   a.no_pivot = h0->pivoting ? 0 : 1;
   a.smem_K = Kmax;
   a.smem_I = std::max(Imax, 1);
-  a.smem_F = Fmax;
   a.queue = static_cast<int*>(h0->d_queue);
   a.perm = nullptr;
   a.phase = nullptr;
@@ -791,7 +791,7 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
   }
   chem_status s = chem_internal_prepare_learned(h0, jobs, n_jobs, &a, st);
   if (s != CHEM_OK) return s;
-  const size_t smem = smem_bytes(a.smem_K, a.smem_I, a.smem_F, h0->precision);
+  const size_t smem = smem_bytes(a.smem_K, a.smem_I, h0->precision);
   if (smem > 227 * 1024) {
     h0->err = "chem_integrate: mechanism too large for shared memory";
     return CHEM_ERR_INVALID_ARG;
@@ -799,7 +799,7 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
   // the mixed form may keep its FP64 matrix in global memory on persistent grids when
   // that lets more CTAs share an SM (large mechanisms)
   const bool m0g_ok = h0->precision == PREC_MIXED && a.sched != SCHED_PLAIN;
-  int block = h0->block ? h0->block : chem_internal_pick_block(h0, a.smem_K, a.smem_I, a.smem_F, m0g_ok);
+  int block = h0->block ? h0->block : chem_internal_pick_block(h0, a.smem_K, a.smem_I, m0g_ok);
   if (h0->autotune) {
     s = chem_internal_autotune(h0, a, st, &block);
     if (s != CHEM_OK) return s;
@@ -810,11 +810,11 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
     grid = (int)total;
   } else {
     int occ = 0;
-    CHEM_CUDA(h0, occupancy_integrate(block, h0->precision, a.smem_K, a.smem_I, a.smem_F, &occ));
+    CHEM_CUDA(h0, occupancy_integrate(block, h0->precision, a.smem_K, a.smem_I, &occ));
     bool m0g = false;
     if (m0g_ok) {
       int occ_g = 0;
-      CHEM_CUDA(h0, occupancy_integrate(block, h0->precision, a.smem_K, a.smem_I, a.smem_F, &occ_g, true));
+      CHEM_CUDA(h0, occupancy_integrate(block, h0->precision, a.smem_K, a.smem_I, &occ_g, true));
       if (occ_g > occ) {
         occ = occ_g;
         m0g = true;
@@ -869,16 +869,16 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
 
 // Block size with the most resident warps per SM for this mechanism size and
 // precision (ties: 128, then 64, then 256 threads).
-int chem_internal_pick_block(chem_handle h, int K, int I, int F, bool allow_m0_global) {
+int chem_internal_pick_block(chem_handle h, int K, int I, bool allow_m0_global) {
   int best = 128, best_w = -1;
   for (int b : {128, 64, 256}) {
     int occ = 0;
-    if (occupancy_integrate(b, h->precision, K, I, F, &occ) != cudaSuccess) {
+    if (occupancy_integrate(b, h->precision, K, I, &occ) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
     int occ_g = 0;
-    if (allow_m0_global && occupancy_integrate(b, h->precision, K, I, F, &occ_g, true) == cudaSuccess)
+    if (allow_m0_global && occupancy_integrate(b, h->precision, K, I, &occ_g, true) == cudaSuccess)
       occ = std::max(occ, occ_g);
     cudaGetLastError();
     if (occ * b / 32 > best_w) {

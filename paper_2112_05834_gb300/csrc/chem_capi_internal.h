@@ -121,7 +121,7 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
                                     cudaStream_t st);
 chem_status chem_internal_launch(chem_handle h, const chem::IntegrateArgs& a, int block, int grid,
                                  cudaStream_t st);
-int chem_internal_pick_block(chem_handle h, int K, int I, int F, bool allow_m0_global = false);
+int chem_internal_pick_block(chem_handle h, int K, int I, bool allow_m0_global = false);
 chem_status chem_internal_graph_launch(chem_handle h, const chem::IntegrateArgs& a, int block, int grid,
                                        cudaStream_t st);
 chem_status chem_internal_autotune(chem_handle h, const chem::IntegrateArgs& a, cudaStream_t st, int* block);

@@ -380,25 +380,23 @@ struct Policy<PREC_FP32ASM> {
 // ---------------------------------------------------------------------------
 struct Layout {
   int nmax, ld;            // matrix dimension bound and leading dimension (odd)
-  int Kmax, Imax, Fmax;
-  size_t off_vec, off_sp, off_fo, off_rx, off_M, off_M0, off_piv, off_red, off_tab, total;
+  int Kmax, Imax;
+  size_t off_vec, off_sp, off_rx, off_M, off_M0, off_piv, off_red, off_tab, total;
 };
 
 __host__ __device__ inline int odd_ld(int n) { return n | 1; }
 
 // vectors (double): y, yn, ys, f0, fv, rr, u[6], sc  -> 13 n
 // species (double): C, hRT, cpR, eg, dcp, dk, akT, ek, ieg -> 9 K
-// Troe slots (double): log10 Fc, (dFc/dT)/Fc -> 2 F
 // reactions (double): q, D, dTc, P, dqs[4] -> 8 I
 // m0_global: the mixed form's FP64 assembled matrix lives in a global-memory slot of
 // the CTA instead of shared memory (large mechanisms, persistent schedulers).
-__host__ __device__ inline Layout make_layout(int Kmax, int Imax, int Fmax, int prec, bool m0_global = false) {
+__host__ __device__ inline Layout make_layout(int Kmax, int Imax, int prec, bool m0_global = false) {
   Layout L;
   L.nmax = Kmax + 1;
   L.ld = odd_ld(L.nmax);
   L.Kmax = Kmax;
   L.Imax = Imax;
-  L.Fmax = Fmax;
   size_t o = 0;
   L.off_red = o;
   o += 64 * sizeof(double);
@@ -408,8 +406,6 @@ __host__ __device__ inline Layout make_layout(int Kmax, int Imax, int Fmax, int 
   o += (size_t)13 * L.nmax * sizeof(double);
   L.off_sp = o;
   o += (size_t)9 * Kmax * sizeof(double);
-  L.off_fo = o;
-  o += (size_t)2 * Fmax * sizeof(double);
   L.off_rx = o;
   if (prec == PREC_FP64) {
     o += (size_t)8 * Imax * sizeof(double);
@@ -452,8 +448,6 @@ struct Cta {
   double *y, *yn, *ys, *f0, *fv, *rr, *u, *sc;
   // species
   double *C, *hRT, *cpR, *eg, *dcp, *dk, *akT, *ek, *ieg;
-  // Troe slots: temperature-only broadening data from the species phase
-  double *flF, *fdl;
   // reactions
   double *q, *D, *dTc, *P, *dqs;
   void* M;
@@ -488,8 +482,6 @@ struct Cta {
     akT = s + 6 * K;
     ek = s + 7 * K;
     ieg = s + 8 * K;
-    flF = reinterpret_cast<double*>(base + L.off_fo);
-    fdl = flF + L.Fmax;
     double* r = reinterpret_cast<double*>(base + L.off_rx);
     const int I = L.Imax;
     q = r;
@@ -639,41 +631,6 @@ __device__ Scal eval_rhs_t(const DevMech& m, Cta<NW>& c, const double* y, double
     if (FF) reinterpret_cast<ff2*>(c.dk)[k] = ff_split(Ck);
     if (JAC) c.dcp[k] = a[1] + T * (2.0 * a[2] + T * (3.0 * a[3] + T * 4.0 * a[4]));
   }
-  // Falloff work that depends on T only -- k0/kinf for every falloff slot and the
-  // Troe centre Fc with log10 Fc (and dFc/dT / Fc) -- is done here, in the species
-  // phase, by the warps that hold no species, one 32-slot chunk per warp (every
-  // thread when all warps hold species): the reaction phase, which waits for its
-  // slowest warp, then carries only the concentration-dependent part of the
-  // falloff chunks. k0/kinf goes to the slot's rate-of-progress entry q[i], which
-  // the reaction phase reads before overwriting it.
-  {
-    const int n_fo = m.I - m.i_fo0;
-    const int wsp = (K + 31) >> 5;  // warps holding species
-    int f = c.tid, stride = NT;
-    if (wsp < NW) {
-      f = c.warp >= wsp ? 32 * (c.warp - wsp) + c.lane : n_fo;
-      stride = 32 * (NW - wsp);
-    }
-    for (; f < n_fo; f += stride) {
-      const int i = m.i_fo0 + f;
-      const double* fo = m.fo + 8 * f;
-      c.q[i] = xexp(fo[0] + fo[1] * logT - fo[2] * invT, c.etab);  // k0 / kinf
-      if (i >= m.i_troe0) {
-        const double alpha = fo[3];
-        // fo[4] = 1/T***, fo[5] = 1/T*
-        const double e3 = xexp(-T * fo[4], c.etab), e1 = xexp(-T * fo[5], c.etab);
-        double Fc = (1.0 - alpha) * e3 + alpha * e1;
-        double dFc = -(1.0 - alpha) * fo[4] * e3 - alpha * fo[5] * e1;
-        if (fo[6] > 0.0) {
-          const double e2 = xexp(-fo[6] * invT, c.etab);
-          Fc += e2;
-          dFc += fo[6] * invT * invT * e2;
-        }
-        c.flF[i - m.i_troe0] = xlog(Fc) * kInvLn10;
-        if (JAC) c.fdl[i - m.i_troe0] = dFc * xrcp(Fc);
-      }
-    }
-  }
   __syncthreads();
   const double cRT = kRc * T / kP0;  // (P0 / (Rc T))^-1
   const double icRT = kP0 * invT / kRc;
@@ -735,13 +692,23 @@ __device__ Scal eval_rhs_t(const DevMech& m, Cta<NW>& c, const double* y, double
     }
     if (i >= m.i_fo0) {
       // fo[0..2] hold the low-pressure minus the high-pressure Arrhenius parameters,
-      // so one exponential gives k0 / kinf (evaluated in the species phase)
+      // so one exponential gives k0 / kinf
       const double* fo = m.fo + 8 * (i - m.i_fo0);
-      const double r0 = c.q[i];  // k0 / kinf
+      const double r0 = xexp(fo[0] + fo[1] * logT - fo[2] * invT, c.etab);  // k0 / kinf
       const double Pr = r0 * Mc;
       double F = 1.0, dlgF_dL = 0.0, dlnF_dT = 0.0;
       if (i >= m.i_troe0) {
-        const double lF = c.flF[i - m.i_troe0];  // log10 Fc (species phase)
+        const double alpha = fo[3];
+        // fo[4] = 1/T***, fo[5] = 1/T*
+        const double e3 = xexp(-T * fo[4], c.etab), e1 = xexp(-T * fo[5], c.etab);
+        double Fc = (1.0 - alpha) * e3 + alpha * e1;
+        double dFc = -(1.0 - alpha) * fo[4] * e3 - alpha * fo[5] * e1;
+        if (fo[6] > 0.0) {
+          const double e2 = xexp(-fo[6] * invT, c.etab);
+          Fc += e2;
+          dFc += fo[6] * invT * invT * e2;
+        }
+        const double lF = xlog(Fc) * kInvLn10;
         const double cc = -0.4 - 0.67 * lF, nn = 0.75 - 1.27 * lF;
         const double x = xlog(Pr) * kInvLn10 + cc;
         const double iden = xrcp(nn - 0.14 * x);
@@ -755,7 +722,7 @@ __device__ Scal eval_rhs_t(const DevMech& m, Cta<NW>& c, const double* y, double
           const double df1_dlF = (-0.67 - f1 * (-1.27 + 0.14 * 0.67)) * iden;
           dlgF_dL = -2.0 * lgF * ig * f1 * df1_dL;
           const double dlgF_dlF = ig - 2.0 * lgF * ig * f1 * df1_dlF;
-          dlnF_dT = dlgF_dlF * c.fdl[i - m.i_troe0];  // d ln F / dT at fixed Pr
+          dlnF_dT = dlgF_dlF * dFc * xrcp(Fc);  // d ln F / dT at fixed Pr
         }
       }
       const double red1 = xrcp(1.0 + Pr);
@@ -1728,7 +1695,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? (PREC == PREC_MIXED ? 5 : 4
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ long long s_work;
   const bool m0g = PREC == PREC_MIXED && args.m0_scratch != nullptr;
-  const Layout L = make_layout(args.smem_K, args.smem_I, args.smem_F, PREC, m0g);
+  const Layout L = make_layout(args.smem_K, args.smem_I, PREC, m0g);
   Cta<NW> c;
   c.bind(smem, L);
   if (m0g) c.M0 = args.m0_scratch + (size_t)blockIdx.x * args.m0_stride;
@@ -1764,7 +1731,7 @@ static cudaError_t prep(KernelT k, size_t smem) {
 
 template <int NW, int PREC, int MTH>
 static cudaError_t launch_integrate_m(const IntegrateArgs& a, int grid, cudaStream_t st) {
-  const size_t smem = smem_bytes(a.smem_K, a.smem_I, a.smem_F, PREC, a.m0_scratch != nullptr);
+  const size_t smem = smem_bytes(a.smem_K, a.smem_I, PREC, a.m0_scratch != nullptr);
   cudaError_t e = prep(k_integrate<NW, PREC, MTH>, smem);
   if (e != cudaSuccess) return e;
   k_integrate<NW, PREC, MTH><<<grid, NW * 32, smem, st>>>(a);

@@ -122,7 +122,7 @@ struct IntegrateArgs {
   int h0_guard;        // 1: keep a supplied initial step inside the starting-step envelope
   int jac_fd;          // FP64 form only: 1 = forward-difference Jacobian (n extra RHS evaluations)
   int no_pivot;        // FP64 form only: 1 = Gaussian elimination without row interchanges
-  int smem_K, smem_I, smem_F;  // sizes the shared-memory carve-up was computed for (F: Troe slots)
+  int smem_K, smem_I;  // sizes the shared-memory carve-up was computed for
   unsigned long long* phase;  // optional [8] per-phase cycle counters (diagnostic)
   double* m0_scratch;  // mixed form, persistent grids: per-CTA slots for the FP64 assembled
   int64_t m0_stride;   //   matrix (null: it stays in shared memory); doubles per slot

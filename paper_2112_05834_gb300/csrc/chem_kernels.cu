@@ -6,8 +6,8 @@
 
 namespace chem {
 
-size_t smem_bytes(int Kmax, int Imax, int Fmax, int prec, bool m0_global) {
-  return make_layout(Kmax, Imax, Fmax, prec, m0_global).total;
+size_t smem_bytes(int Kmax, int Imax, int prec, bool m0_global) {
+  return make_layout(Kmax, Imax, prec, m0_global).total;
 }
 
 // W-method instantiations (chem_kernels_w.cu)
@@ -28,7 +28,7 @@ template <int NW, int PREC>
 __global__ void __launch_bounds__(NW * 32) k_diag(const __grid_constant__ DiagArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   using A = typename Policy<PREC>::ASM;
-  const Layout L = make_layout(a.m.K, a.m.I, a.m.I - a.m.i_troe0, PREC);
+  const Layout L = make_layout(a.m.K, a.m.I, PREC);
   Cta<NW> c;
   c.bind(smem, L);
   c.load_tables();
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(NW * 32) k_lu_solve(const __grid_constant__ Lu
   extern __shared__ __align__(16) unsigned char smem[];
   using P = Policy<PREC>;
   using R = typename P::LU;
-  const Layout L = make_layout(a.dim - 1, 1, 0, PREC);
+  const Layout L = make_layout(a.dim - 1, 1, PREC);
   Cta<NW> c;
   c.bind(smem, L);
   constexpr int NT = NW * 32;
@@ -128,8 +128,8 @@ cudaError_t launch_integrate(const IntegrateArgs& a, int block, int prec, int gr
 #undef LI
 }
 
-cudaError_t occupancy_integrate(int block, int prec, int K, int I, int F, int* ctas_per_sm, bool m0_global) {
-  const size_t smem = smem_bytes(K, I, F, prec, m0_global);
+cudaError_t occupancy_integrate(int block, int prec, int K, int I, int* ctas_per_sm, bool m0_global) {
+  const size_t smem = smem_bytes(K, I, prec, m0_global);
   cudaError_t e;
 #define OCC(NW, P)                                                                                    \
   do {                                                                                                \
@@ -175,7 +175,7 @@ cudaError_t launch_diag(const DevMech& m, int64_t n, const double* T, const doub
   a.rtol = rtol;
   a.atol = atol;
   a.what = what;
-  const size_t smem = smem_bytes(m.K, m.I, m.I - m.i_troe0, prec);
+  const size_t smem = smem_bytes(m.K, m.I, prec);
   const int grid = (int)(n < 65535 ? n : 65535);
   if (prec == PREC_FP64) return launch_simple<PREC_FP64>(k_diag<4, PREC_FP64>, a, smem, grid, st);
   if (prec == PREC_MIXED) return launch_simple<PREC_MIXED>(k_diag<4, PREC_MIXED>, a, smem, grid, st);
@@ -199,7 +199,7 @@ cudaError_t launch_lu_solve(int64_t n_mat, int dim, const double* A, const doubl
   a.x = x;
   a.info = info;
   a.ir = ir;
-  const size_t smem = smem_bytes(dim - 1, 1, 0, prec);
+  const size_t smem = smem_bytes(dim - 1, 1, prec);
   const int grid = (int)(n_mat < 65535 ? n_mat : 65535);
   if (prec == PREC_FP64) return launch_simple<PREC_FP64>(k_lu_solve<4, PREC_FP64>, a, smem, grid, st);
   if (prec == PREC_MIXED) return launch_simple<PREC_MIXED>(k_lu_solve<4, PREC_MIXED>, a, smem, grid, st);

@@ -10,9 +10,9 @@
 
 namespace chem {
 
-size_t smem_bytes(int Kmax, int Imax, int Fmax, int prec, bool m0_global = false);
+size_t smem_bytes(int Kmax, int Imax, int prec, bool m0_global = false);
 cudaError_t launch_integrate(const IntegrateArgs& a, int block, int prec, int grid, cudaStream_t st);
-cudaError_t occupancy_integrate(int block, int prec, int K, int I, int F, int* ctas_per_sm, bool m0_global = false);
+cudaError_t occupancy_integrate(int block, int prec, int K, int I, int* ctas_per_sm, bool m0_global = false);
 cudaError_t launch_diag(const DevMech& m, int64_t n, const double* T, const double* p, const double* Y,
                         double* out, double dt, double rtol, double atol, int what, int prec,
                         cudaStream_t st, int jac_fd = 0, int q = 4);

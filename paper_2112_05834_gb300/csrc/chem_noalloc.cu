@@ -130,14 +130,13 @@ extern "C" chem_status chem_integrate_noalloc(chem_handle h, int64_t n_cells, do
   a.tab = chem::method_tableau(h->method);
   a.smem_K = h->K;
   a.smem_I = h->I > 0 ? h->I : 1;
-  a.smem_F = h->dm.I - h->dm.i_troe0;
-  const int block = h->block ? h->block : chem_internal_pick_block(h, a.smem_K, a.smem_I, a.smem_F);
+  const int block = h->block ? h->block : chem_internal_pick_block(h, a.smem_K, a.smem_I);
   int grid;
   if (a.sched == chem::SCHED_PLAIN) {
     grid = (int)n_cells;
   } else {
     int occ = 0;
-    cudaError_t e = chem::occupancy_integrate(block, h->precision, a.smem_K, a.smem_I, a.smem_F, &occ);
+    cudaError_t e = chem::occupancy_integrate(block, h->precision, a.smem_K, a.smem_I, &occ);
     if (e != cudaSuccess || occ < 1) {
       h->err = "chem_integrate_noalloc: kernel does not fit on an SM";
       return CHEM_ERR_CUDA;

@@ -187,7 +187,7 @@ chem_status chem_internal_graph_launch(chem_handle h, const IntegrateArgs& a, in
       }
     }
     int occ = 0;
-    occupancy_integrate(block, h->precision, a.smem_K, a.smem_I, a.smem_F, &occ, a.m0_scratch != nullptr);  // sets kernel attributes
+    occupancy_integrate(block, h->precision, a.smem_K, a.smem_I, &occ, a.m0_scratch != nullptr);  // sets kernel attributes
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess && a.sched == SCHED_QUEUE && !h->queue_preset)
@@ -291,7 +291,7 @@ chem_status chem_internal_autotune(chem_handle h, const IntegrateArgs& a, cudaSt
     t.m0_scratch = nullptr;         // trials keep the FP64 matrix in shared memory
     t.jobs[0].h0 = nullptr;
     int occ = 0;
-    if (occupancy_integrate(b, h->precision, a.smem_K, a.smem_I, a.smem_F, &occ) != cudaSuccess || occ < 1) continue;
+    if (occupancy_integrate(b, h->precision, a.smem_K, a.smem_I, &occ) != cudaSuccess || occ < 1) continue;
     const int grid = (int)std::min<int64_t>(S, (int64_t)occ * h->num_sms);
     float ms_total = 0.0f;
     for (int rep = 0; rep < 2; ++rep) {
