@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(NW * 32) k_diag(const __grid_constant__ DiagAr
   const Layout L = make_layout(a.m.K, a.m.I, PREC);
   Cta<NW> c;
   c.bind(smem, L);
-  c.load_tables();
+
   constexpr int NT = NW * 32;
   const int K = a.m.K, n = K + 1, ld = odd_ld(n);
   for (int64_t cell = blockIdx.x; cell < a.n; cell += gridDim.x) {
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(NW * 32) k_diag(const __grid_constant__ DiagAr
 // The rate kernels' elementary functions, elementwise (diagnostic): op 0 exp, 1 log, 2 1/x.
 __global__ void k_math(int op, const double* x, double* y, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = op == 0 ? xexp(x[i], g_exp2_tab) : op == 1 ? xlog(x[i]) : xrcp(x[i]);
+    y[i] = op == 0 ? xexp(x[i]) : op == 1 ? xlog(x[i]) : xrcp(x[i]);
 }
 
 struct LuArgs {
