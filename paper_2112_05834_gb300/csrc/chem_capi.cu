@@ -680,7 +680,8 @@ extern "C" chem_status chem_set_option(chem_handle h, const char* key, double va
       return CHEM_ERR_INVALID_ARG;
     }
     h->*(o.field) = (int)value;
-    if (std::strcmp(key, "block") == 0) h->autotuned_key = -1;  // explicit choice wins
+    if (std::strcmp(key, "block") == 0 || std::strcmp(key, "precision") == 0 || std::strcmp(key, "method") == 0)
+      h->autotuned_key = -1;  // explicit choice wins; a new kernel is tuned afresh
     return CHEM_OK;
   }
   h->err = std::string("chem_set_option: unknown key ") + key;
@@ -800,8 +801,9 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
   // that lets more CTAs share an SM (large mechanisms)
   const bool m0g_ok = h0->precision == PREC_MIXED && a.sched != SCHED_PLAIN;
   int block = h0->block ? h0->block : chem_internal_pick_block(h0, a.smem_K, a.smem_I, m0g_ok);
+  int tuned_ctas = 0, tuned_m0g = -1;  // the autotuner's resident CTAs per SM and matrix layout
   if (h0->autotune) {
-    s = chem_internal_autotune(h0, a, st, &block);
+    s = chem_internal_autotune(h0, a, st, &block, &tuned_ctas, &tuned_m0g);
     if (s != CHEM_OK) return s;
   }
   h0->last_block = block;
@@ -815,11 +817,12 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
     if (m0g_ok) {
       int occ_g = 0;
       CHEM_CUDA(h0, occupancy_integrate(block, h0->precision, a.smem_K, a.smem_I, &occ_g, true));
-      if (occ_g > occ) {
+      if (tuned_m0g >= 0 ? tuned_m0g == 1 : occ_g > occ) {
         occ = occ_g;
         m0g = true;
       }
     }
+    if (tuned_ctas > 0) occ = std::min(occ, tuned_ctas);
     if (occ < 1) {
       h0->err = "chem_integrate: kernel does not fit on an SM";
       return CHEM_ERR_CUDA;

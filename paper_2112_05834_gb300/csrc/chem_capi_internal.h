@@ -93,9 +93,11 @@ struct chem_handle_s {
   int64_t rm_cap = 0;
   int64_t rm_last_n = -1;         // cells of the last mapped call (-1: last call unmapped)
   bool queue_preset = false;      // the next launch keeps the queue's start (set by the mapping)
-  // autotuner cache: key -> block
+  // autotuner cache: key -> (block, resident CTAs per SM, matrix layout)
   long long autotuned_key = -1;
   int autotuned_block = 128;
+  int autotuned_ctas = 0;   // 0: as many as fit
+  int autotuned_m0g = -1;   // mixed form's FP64 matrix: 0 shared memory, 1 global slot, -1 automatic
   std::string err;
 };
 
@@ -124,7 +126,8 @@ chem_status chem_internal_launch(chem_handle h, const chem::IntegrateArgs& a, in
 int chem_internal_pick_block(chem_handle h, int K, int I, bool allow_m0_global = false);
 chem_status chem_internal_graph_launch(chem_handle h, const chem::IntegrateArgs& a, int block, int grid,
                                        cudaStream_t st);
-chem_status chem_internal_autotune(chem_handle h, const chem::IntegrateArgs& a, cudaStream_t st, int* block);
+chem_status chem_internal_autotune(chem_handle h, const chem::IntegrateArgs& a, cudaStream_t st, int* block,
+                                   int* ctas, int* m0g);
 chem_status chem_internal_prepare_learned(chem_handle h, const chem_job* jobs, int32_t n_jobs,
                                           chem::IntegrateArgs* a, cudaStream_t st);
 void chem_internal_release_learned(chem_handle h);

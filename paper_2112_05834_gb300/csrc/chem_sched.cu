@@ -224,62 +224,98 @@ static long long tune_key(const chem_handle h, const IntegrateArgs& a) {
          ((long long)a.sched << 16) ^ n_bucket;
 }
 
-static bool cache_lookup(long long key, int* block) {
+static bool cache_lookup(long long key, int* block, int* ctas, int* m0g) {
   const char* path = std::getenv("CHEM_AUTOTUNE_CACHE");
   if (!path) return false;
   std::ifstream f(path);
   long long k;
-  int b;
-  while (f >> k >> b)
-    if (k == key && (b == 64 || b == 128 || b == 256)) {
+  int b, c, g;
+  while (f >> k >> b >> c >> g)
+    if (k == key && (b == 64 || b == 128 || b == 256) && c >= 0 && g >= -1 && g <= 1) {
       *block = b;
+      *ctas = c;
+      *m0g = g;
       return true;
     }
   return false;
 }
 
-static void cache_store(long long key, int block) {
+static void cache_store(long long key, int block, int ctas, int m0g) {
   const char* path = std::getenv("CHEM_AUTOTUNE_CACHE");
   if (!path) return;
   std::ofstream f(path, std::ios::app);
-  f << key << " " << block << "\n";
+  f << key << " " << block << " " << ctas << " " << m0g << "\n";
 }
 
-chem_status chem_internal_autotune(chem_handle h, const IntegrateArgs& a, cudaStream_t st, int* block) {
+// Candidates: CTA size (2, 4 or 8 warps on one cell) x matrix layout of the mixed form
+// (FP64 assembled matrix in shared memory, or in a per-CTA global slot, which leaves room
+// for more CTAs) x resident CTAs per SM on persistent grids (as many as fit, or one
+// fewer: fewer CTAs compete for the SM's FP64 pipe and issue slots). Each is timed on a
+// sample of the call's cells (copies; the caller's arrays are not touched), one warm-up
+// and one timed launch, and the fastest is kept: *block, *ctas (0 = as many as fit) and
+// *m0g (-1 unless the layout was a choice).
+chem_status chem_internal_autotune(chem_handle h, const IntegrateArgs& a, cudaStream_t st, int* block, int* ctas,
+                                   int* m0g) {
   const long long key = tune_key(h, a);
   if (h->autotuned_key == key) {
     *block = h->autotuned_block;
+    *ctas = h->autotuned_ctas;
+    *m0g = h->autotuned_m0g;
     return CHEM_OK;
   }
-  int cached = 0;
-  if (cache_lookup(key, &cached)) {
+  int cb = 0, cc = 0, cg = -1;
+  if (cache_lookup(key, &cb, &cc, &cg)) {
     h->autotuned_key = key;
-    h->autotuned_block = cached;
-    *block = cached;
+    h->autotuned_block = *block = cb;
+    h->autotuned_ctas = *ctas = cc;
+    h->autotuned_m0g = *m0g = cg;
     return CHEM_OK;
   }
   if (a.n_jobs != 1 || a.perm) return CHEM_OK;  // tune single-job, index-ordered calls only (keep *block)
   const Job& J = a.jobs[0];
   const int64_t S = std::min<int64_t>(J.n_cells, 4 * 1024);
   const int K = J.m.K;
+  const bool persistent = a.sched != SCHED_PLAIN;
+  const bool layouts = persistent && h->precision == PREC_MIXED;
+  // candidates and the largest grid any of them needs (for the matrix slots)
+  struct Cand { int b, g, c; };
+  std::vector<Cand> cands;
+  int64_t max_grid = 1;
+  for (int b : {64, 128, 256})
+    for (int g = 0; g <= (layouts ? 1 : 0); ++g) {
+      int occ = 0;
+      if (occupancy_integrate(b, h->precision, a.smem_K, a.smem_I, &occ, g == 1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      if (occ < 1) continue;
+      for (int c = occ; c >= (persistent ? std::max(1, occ - 1) : occ); --c) {
+        cands.push_back({b, g, c});
+        max_grid = std::max<int64_t>(max_grid, std::min<int64_t>(S, (int64_t)c * h->num_sms));
+      }
+    }
+  if (cands.empty()) return CHEM_OK;
+  const int64_t stride = (int64_t)(a.smem_K + 1) * ((a.smem_K + 1) | 1);
+  const size_t sample_doubles = (size_t)S * (K + 2) * 2;
+  const size_t slot_doubles = layouts ? (size_t)max_grid * stride : 0;
   double* buf = nullptr;
-  cudaError_t e = cudaMalloc(&buf, (size_t)S * (K + 2) * sizeof(double) * 2);
+  cudaError_t e = cudaMalloc(&buf, (sample_doubles + slot_doubles) * sizeof(double));
   if (e != cudaSuccess) {
     h->err = std::string("autotune: ") + cudaGetErrorString(e);
     return CHEM_ERR_OOM;
   }
   double *T0 = buf, *p0 = buf + S, *Y0 = buf + 2 * S;
   double* work = buf + (size_t)S * (K + 2);
+  double* slots = buf + sample_doubles;
   cudaMemcpyAsync(T0, J.T, S * 8, cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(p0, J.p, S * 8, cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(Y0, J.Y, (size_t)S * K * 8, cudaMemcpyDeviceToDevice, st);
   cudaEvent_t ev0, ev1;
   cudaEventCreate(&ev0);
   cudaEventCreate(&ev1);
-  const int cands[3] = {64, 128, 256};
   float best = 1e30f;
-  int best_b = *block;
-  for (int b : cands) {
+  Cand best_c{*block, -1, 0};
+  for (const Cand& cd : cands) {
     IntegrateArgs t = a;
     t.n_total = S;
     t.jobs[0].n_cells = S;
@@ -288,17 +324,16 @@ chem_status chem_internal_autotune(chem_handle h, const IntegrateArgs& a, cudaSt
     t.jobs[0].Y = work + 2 * S;
     t.jobs[0].cost_out = nullptr;
     t.jobs[0].st.h_last = nullptr;  // keep the carried-over steps of the real call intact
-    t.m0_scratch = nullptr;         // trials keep the FP64 matrix in shared memory
     t.jobs[0].h0 = nullptr;
-    int occ = 0;
-    if (occupancy_integrate(b, h->precision, a.smem_K, a.smem_I, &occ) != cudaSuccess || occ < 1) continue;
-    const int grid = (int)std::min<int64_t>(S, (int64_t)occ * h->num_sms);
+    t.m0_scratch = cd.g == 1 ? slots : nullptr;
+    t.m0_stride = cd.g == 1 ? stride : 0;
+    const int grid = persistent ? (int)std::min<int64_t>(S, (int64_t)cd.c * h->num_sms) : (int)S;
     float ms_total = 0.0f;
     for (int rep = 0; rep < 2; ++rep) {
       cudaMemcpyAsync(work, T0, (size_t)S * (K + 2) * 8, cudaMemcpyDeviceToDevice, st);
       if (t.sched == SCHED_QUEUE) cudaMemsetAsync(t.queue, 0, sizeof(int), st);
       cudaEventRecord(ev0, st);
-      launch_integrate(t, b, h->precision, t.sched == SCHED_PLAIN ? (int)S : grid, st);
+      launch_integrate(t, cd.b, h->precision, grid, st);
       cudaEventRecord(ev1, st);
       cudaEventSynchronize(ev1);
       float ms = 0.0f;
@@ -307,7 +342,7 @@ chem_status chem_internal_autotune(chem_handle h, const IntegrateArgs& a, cudaSt
     }
     if (ms_total < best) {
       best = ms_total;
-      best_b = b;
+      best_c = cd;
     }
   }
   cudaEventDestroy(ev0);
@@ -319,10 +354,16 @@ chem_status chem_internal_autotune(chem_handle h, const IntegrateArgs& a, cudaSt
     h->err = std::string("autotune: ") + cudaGetErrorString(e);
     return CHEM_ERR_CUDA;
   }
+  const int tuned_m0g = layouts ? best_c.g : -1;
+  const int tuned_ctas = persistent ? best_c.c : 0;
   h->autotuned_key = key;
-  h->autotuned_block = best_b;
-  cache_store(key, best_b);
-  *block = best_b;
+  h->autotuned_block = best_c.b;
+  h->autotuned_ctas = tuned_ctas;
+  h->autotuned_m0g = tuned_m0g;
+  cache_store(key, best_c.b, tuned_ctas, tuned_m0g);
+  *block = best_c.b;
+  *ctas = tuned_ctas;
+  *m0g = tuned_m0g;
   return CHEM_OK;
 }
 

@@ -502,12 +502,18 @@ OXZONE_CLASSES = ((0.4, "oxidiser", 795.0, 805.0), (0.36, "unreacted", 700.0, 90
                   (0.18, "igniting", 1000.0, 1600.0), (0.06, "burnt", 2000.0, 2700.0))
 
 
-def perturb_states(states: CellStates, seed: int, dT: float = 50.0, w_max: float = 0.1):
-    """Mixing perturbation between CFD steps: T += U[-dT, dT];
+def perturb_states(states: CellStates, seed: int, dT: float = 50.0, w_max: float = 0.1,
+                   T_range=(300.0, 3000.0)):
+    """Mixing perturbation between CFD steps: T += U[-dT, dT], reflected at the ends of
+    T_range (the NASA fits' range: over many steps the perturbation is a random walk,
+    which would otherwise carry a few of a million cells out of it);
     Y <- (1 - w) Y + w Y_partner with a seeded random partner cell and w ~ U[0, w_max]."""
     rng = np.random.default_rng(seed)
     n = states.T.shape[0]
     T = states.T + rng.uniform(-dT, dT, size=n)
+    lo, hi = T_range
+    T = np.where(T < lo, 2.0 * lo - T, T)
+    T = np.where(T > hi, 2.0 * hi - T, T)
     partner = rng.integers(0, n, size=n)
     w = rng.uniform(0.0, w_max, size=(n, 1))
     Y = (1.0 - w) * states.Y + w * states.Y[partner]

@@ -571,13 +571,22 @@ def test_full_size_c100_mixed_sampled_parity(pkg, orc, ir):
 
 
 def test_autotune_picks_a_block_and_keeps_parity(pkg, orc, tmp_path, monkeypatch):
-    """The autotuner times block sizes on a sample of the call's cells (copies) and
-    keeps the fastest; the caller's cells are integrated once, within the bound, and
-    the choice is cached (in the handle and in the cache file)."""
+    """The autotuner times CTA size x matrix layout x resident CTAs per SM on a sample
+    of the call's cells (copies) and keeps the fastest; the caller's cells are
+    integrated once, within the bound, and the choice is cached (in the handle and in
+    the cache file, one "key block ctas layout" line); a second handle reads the file
+    instead of timing and integrates bitwise identically."""
     cache = tmp_path / "autotune.txt"
     monkeypatch.setenv("CHEM_AUTOTUNE_CACHE", str(cache))
     m, st, dt, ref = _oracle_ref(orc, "c54_65k", 333)
     g = _run(pkg, m, st, dt, precision=1, autotune=1)
     _assert_bound(g["T"], g["Y"], ref, "autotune")
-    lines = cache.read_text().split()
-    assert len(lines) == 2 and int(lines[1]) in (64, 128, 256)
+    f = cache.read_text().split()
+    assert len(f) == 4, f
+    block, ctas, layout = int(f[1]), int(f[2]), int(f[3])
+    assert block in (64, 128, 256) and 1 <= ctas <= 16 and layout in (0, 1)
+    print("autotuned: block", block, "CTAs per SM", ctas, "matrix in", "global slot" if layout else "shared memory")
+    g2 = _run(pkg, m, st, dt, precision=1, autotune=1)
+    assert len(cache.read_text().split()) == 4  # read, not re-timed
+    np.testing.assert_array_equal(g2["T"], g["T"])
+    np.testing.assert_array_equal(g2["Y"], g["Y"])

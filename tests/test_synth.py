@@ -93,3 +93,17 @@ def test_perturb_keeps_sum():
     st2 = synth.perturb_states(st, seed=9)
     np.testing.assert_allclose(st2.Y.sum(axis=1), 1.0, atol=1e-14)
     assert np.abs(st2.T - st.T).max() <= 50.0
+
+
+def test_perturb_reflects_temperature_into_range():
+    """Repeated perturbation is a random walk in T; it stays within [300, 3000] K by
+    reflection, and a step that stays inside the range is a plain shift."""
+    m = synth.mechanism_preset("h2_10")
+    st = synth.gen_states(m, 4096, seed=4, p=synth.ATM, classes=((1.0, "unreacted", 310.0, 330.0),))
+    for s in range(40):
+        st = synth.perturb_states(st, seed=s)
+        assert st.T.min() >= 300.0 and st.T.max() <= 3000.0
+    st0 = synth.gen_states(m, 64, seed=5, p=synth.ATM, classes=((1.0, "unreacted", 1000.0, 1100.0),))
+    st1 = synth.perturb_states(st0, seed=1)
+    d = st1.T - st0.T
+    assert np.all(np.abs(d) <= 50.0)
