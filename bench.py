@@ -183,14 +183,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def kernel_source_digest():
+    """sha256 over the integration kernel's device source (the shared device header and
+    the translation unit that instantiates the RODAS4 stepper), in that order."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("chem_device.cuh", "chem_kernels.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2112_05834_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def kernel_traffic(n_cells):
     """DRAM bytes per launch of the integration kernel from the committed ncu summary
     (profiles/k_integrate_traffic.txt), scaled from the captured batch to n_cells (state
     traffic is per cell); None when the kernel source changed since the capture."""
-    import hashlib
-
     path = os.path.join(ROOT, "profiles", "k_integrate_traffic.txt")
-    src = os.path.join(ROOT, "paper_2112_05834_gb300", "csrc", "chem_kernels.cu")
     if not os.path.exists(path):
         return None
     kv = {}
@@ -198,8 +206,7 @@ def kernel_traffic(n_cells):
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if kv.get("kernel_source_sha256") != digest:
+    if kv.get("kernel_source_sha256") != kernel_source_digest():
         return None
     per_cell = (float(kv["dram_bytes_read"]) + float(kv["dram_bytes_write"])) / float(kv["cells"])
     return per_cell * n_cells
