@@ -79,6 +79,10 @@ def parse():
     ap.add_argument("--no-h0-guard", action="store_true",
                     help="with --cfd-loop: the learned initial step as predicted, without the starting-step "
                          "envelope check (option h0_guard = 0)")
+    ap.add_argument("--diag-h0", action="store_true",
+                    help="with --cfd-loop: per step, the error |ln(h0 / h_first)| of the learned and of the "
+                         "heuristic initial step against the first accepted step, for cells whose standardised "
+                         "features lie within / beyond 5 training standard deviations")
     ap.add_argument("--no-learned-order", action="store_true",
                     help="with --cfd-loop: learned initial step only, index order")
     ap.add_argument("--refmap", action="store_true",
@@ -753,6 +757,26 @@ def run_cfd_loop(args):
             model.attach(learned)
             logs.clear()
         T, Y, ms, s = timed(plain, T0, p, Y0)
+        if args.diag_h0 and step >= 6:
+            # initial-step errors against the plain form's first accepted steps (same inputs)
+            hf = s["h_first"].cpu().numpy()
+            ok = (s["status"].cpu().numpy() == 0) & (hf > 0)
+            h_heur = plain.eval_h0(T0, p, Y0, dt, RTOL, ATOL).cpu().numpy()
+            lc, lh = model.predict(T0, p, Y0)
+            h_pred = np.clip(np.exp(lh.cpu().numpy().astype(np.float64)), 1e-14, dt)
+            prm = model.get_params()
+            D = m.n_species + 2
+            mu, sd = prm[:D].astype(np.float64), prm[D:2 * D].astype(np.float64)
+            x = np.concatenate([(st.T / 1000.0)[:, None], np.log(st.p)[:, None], np.log(st.Y + 1e-20)], axis=1)
+            ood = (np.abs((x - mu) / sd) > 5.0).any(axis=1)
+            e_l = np.abs(np.log(h_pred / np.where(ok, hf, 1.0)))
+            e_h = np.abs(np.log(np.clip(h_heur, 1e-300, None) / np.where(ok, hf, 1.0)))
+            line["diag_h0"] = {"ood_fraction": float(ood[ok].mean()),
+                               "learned_err_in": float(np.median(e_l[ok & ~ood])) if (ok & ~ood).any() else None,
+                               "learned_err_ood": float(np.median(e_l[ok & ood])) if (ok & ood).any() else None,
+                               "heuristic_err_in": float(np.median(e_h[ok & ~ood])) if (ok & ~ood).any() else None,
+                               "heuristic_err_ood": float(np.median(e_h[ok & ood])) if (ok & ood).any() else None,
+                               "learned_shorter_frac": float((h_pred[ok] < hf[ok]).mean())}
         line.update({"plain_ms": ms, "plain_substeps": int(s["substeps"].sum()),
                      "plain_rejects": int(s["rejects"].sum()), "plain_failed": int((s["status"] != 0).sum())})
         if step <= 5:
