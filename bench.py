@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--no-h0-guard", action="store_true",
                     help="with --cfd-loop: the learned initial step as predicted, without the starting-step "
                          "envelope check (option h0_guard = 0)")
+    ap.add_argument("--h0-range", type=int, default=0,
+                    help="with --cfd-loop: option h0_range (cells with a standardised model input beyond "
+                         "this many training standard deviations start from the heuristic; 0 = off)")
     ap.add_argument("--diag-h0", action="store_true",
                     help="with --cfd-loop: per step, the error |ln(h0 / h_first)| of the learned and of the "
                          "heuristic initial step against the first accepted step, for cells whose standardised "
@@ -746,6 +749,7 @@ def run_cfd_loop(args):
             learned.set_option("order", 0 if args.no_learned_order else 1)
             learned.set_option("h0", 1)
             learned.set_option("h0_guard", 0 if args.no_h0_guard else 1)
+            learned.set_option("h0_range", args.h0_range)
             logs.clear()
         if args.retrain_every and step > 6 and (step - 6) % args.retrain_every == 0 and logs:
             t0 = time.perf_counter()
@@ -797,6 +801,7 @@ def run_cfd_loop(args):
                                   seed=100 + step)
     print(json.dumps({"cfd_loop_summary": "steps 6-20", "n_cells": n, "retrain_every": args.retrain_every,
                       "learned_order": not args.no_learned_order, "h0_guard": not args.no_h0_guard,
+                      "h0_range": args.h0_range,
                       "plain_cells_step_per_s": 15 * n / (tot["plain_ms"] / 1e3),
                       "learned_cells_step_per_s": 15 * n / (tot["learned_ms"] / 1e3),
                       "speedup": tot["plain_ms"] / tot["learned_ms"],

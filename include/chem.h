@@ -216,6 +216,10 @@ chem_status chem_integrate_jobs(const chem_job* jobs, int32_t n_jobs, double dt,
  *                 is kept, at the cell's first step, inside the starting-step
  *                 heuristic's envelope [h_a, 100 h_a], h_a = 0.01 |y0| / |f(y0)| in
  *                 the WRMS norm (no extra RHS evaluation); 0 = taken as supplied
+ *   "h0_range"    with h0 = 1: z > 0 = a cell whose standardised model input has a
+ *                 feature beyond +-z standard deviations of the training data
+ *                 starts from the heuristic instead of the prediction (the model is
+ *                 not trusted outside the states it was trained on); 0 (default) = off
  *   "max_steps"   step budget per cell (default 100000)
  *   "block"       threads per cell: 64, 128 or 256; 0 (default) = the size with
  *                 the most resident warps per SM for the mechanism and precision

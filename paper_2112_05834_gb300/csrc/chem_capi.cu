@@ -665,6 +665,7 @@ static const OptionDef kOptions[] = {
     {"job_launch", &chem_handle_s::job_launch, 0, 1},
     {"method", &chem_handle_s::method, 0, 1},
     {"h0_guard", &chem_handle_s::h0_guard, 0, 1},
+    {"h0_range", &chem_handle_s::h0_range, 0, 1000},
 };
 
 extern "C" chem_status chem_set_option(chem_handle h, const char* key, double value) {

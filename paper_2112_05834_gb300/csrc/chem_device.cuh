@@ -653,7 +653,7 @@ __host__ __device__ inline Layout make_layout(int Kmax, int Imax, int prec, bool
 }
 
 
-// Scalars kept in the reduction area (after the 4 x NW partial-sum slots).
+// Scalars kept in the reduction area (its first 32 slots are unused).
 // SC_OUT: 8 broadcast results of Cta::reduce; SC_PIV: pivot search slots (12 NW bytes)
 // (SC_INVT during the rate evaluation, SC_INVP during the LU: never live together)
 enum { SC_OUT = 32, SC_LOGT = 48, SC_INVT = 49, SC_INVP = 49, SC_FLAG = 50, SC_MISC = 51, SC_PIV = 52 };
@@ -661,7 +661,7 @@ enum { SC_OUT = 32, SC_LOGT = 48, SC_INVT = 49, SC_INVP = 49, SC_FLAG = 50, SC_M
 template <int NW>
 struct Cta {
   static constexpr int NT = NW * 32;
-  static constexpr int SW = NW - 1;  // the warp that finishes reductions and CTA scalars
+  static constexpr int SW = NW - 1;  // the warp that computes CTA scalars (ln T, 1/T, the FP64 solve)
   int tid, lane, warp;
   double* red;
   // vectors
@@ -716,33 +716,55 @@ struct Cta {
   }
 
 
-  // Sum of NV values over the CTA; every thread receives the same totals
-  // (fixed summation order: deterministic). Only the first nw warps may hold
-  // non-zero values (the others skip the shuffle tree). The last warp (SW, which
-  // holds no species in the usual case of fewer species than threads) adds the
-  // per-warp partials and passes the totals to fin(tot, out), which derives NO
-  // scalars from them; lane 0's out[] reaches every thread through shared memory,
-  // so scalar follow-up work (reciprocals, roots) runs on one warp, not all.
+  // Sum of NV (1, 2 or 4) values over the CTA; every thread receives the same
+  // totals (fixed summation order: deterministic). Only the first nw warps may hold
+  // non-zero values, nw = warps_for(count) of a loop over count <= n entries.
+  // The FP64 pipe, shared by the SM's four schedulers, bounds the integration, so
+  // the sum is arranged to issue few FP64 instructions:
+  //  1. each data warp folds its NV values into one value per lane by log2(NV)
+  //     transposing butterfly levels (a lane keeps one of two values and adds the
+  //     partner's half of it), so that lane groups of 32/NV lanes carry one value each;
+  //  2. warps 1..nw-1 leave their lane values in the scratch vector sc (free outside
+  //     the solves; 32 (nw-1) <= count <= n entries), warp 0 adds them lane by lane;
+  //  3. warp 0 finishes the butterfly inside each lane group and passes the totals to
+  //     fin(tot, out), which derives NO scalars from them; lane 0's out[] reaches
+  //     every thread through shared memory, so scalar follow-up work (reciprocals,
+  //     roots) runs on one warp, not all.
+  // With two data warps: 6, 7 and 10 FP64 warp instructions for 1, 2 and 4 values,
+  // against 11, 22 and 44 for one shuffle tree per value and warp.
   template <int NV, int NO, class F>
   __device__ void reduce(const double (&v)[NV], int nw, F fin, double (&out)[NO]) {
-    static_assert(NV * NW <= SC_OUT && NO <= 8, "reduction slots");
+    static_assert(NV == 1 || NV == 2 || NV == 4, "reduce: 1, 2 or 4 values");
+    static_assert(NO <= 8, "reduction slots");
+    constexpr int LV = NV == 1 ? 0 : (NV == 2 ? 1 : 2);  // transposing levels
+    double x = 0.0;
     if (warp < nw) {
-#pragma unroll
-      for (int a = 0; a < NV; ++a) {
-        double x = v[a];
-#pragma unroll
-        for (int o = 16; o; o >>= 1) x += __shfl_down_sync(FULLMASK, x, o);
-        if (lane == 0) red[a * NW + warp] = x;
+      if constexpr (NV == 1) {
+        x = v[0];
+      } else {
+        // level 16: lanes 0-15 keep value 0 (and 2), lanes 16-31 value 1 (and 3)
+        const bool h16 = lane & 16;
+        x = (h16 ? v[1] : v[0]) + __shfl_xor_sync(FULLMASK, h16 ? v[0] : v[1], 16);
+        if constexpr (NV == 4) {
+          const double x2 = (h16 ? v[3] : v[2]) + __shfl_xor_sync(FULLMASK, h16 ? v[2] : v[3], 16);
+          // level 8: lanes with bit 3 clear keep values 0/1, set keep 2/3
+          const bool h8 = lane & 8;
+          x = (h8 ? x2 : x) + __shfl_xor_sync(FULLMASK, h8 ? x : x2, 8);
+        }
       }
+      if (warp > 0) sc[(warp - 1) * 32 + lane] = x;
     }
     __syncthreads();
-    if (warp == SW) {
+    if (warp == 0) {
+      for (int w = 1; w < nw; ++w) x += sc[(w - 1) * 32 + lane];
+#pragma unroll
+      for (int o = 16 >> LV; o; o >>= 1) x += __shfl_xor_sync(FULLMASK, x, o);
       double tot[NV];
 #pragma unroll
       for (int a = 0; a < NV; ++a) {
-        double s = red[a * NW];
-        for (int w = 1; w < nw; ++w) s += red[a * NW + w];
-        tot[a] = s;
+        // value a's lane group: bit 4 = a & 1, bit 3 = a >> 1
+        const int src = NV == 1 ? 0 : (((a & 1) << 4) | ((a >> 1) << 3));
+        tot[a] = NV == 1 ? x : __shfl_sync(FULLMASK, x, src);
       }
       double o[NO];
       fin(tot, o);
@@ -758,7 +780,7 @@ struct Cta {
 
   // Plain CTA sum of NV values (nw as in reduce).
   template <int NV>
-  __device__ void sum(double (&v)[NV], int nw = NW) {
+  __device__ void sum(double (&v)[NV], int nw) {
     reduce(v, nw, [](const double (&t)[NV], double (&o)[NV]) {
 #pragma unroll
       for (int a = 0; a < NV; ++a) o[a] = t[a];
@@ -797,13 +819,12 @@ __device__ Scal eval_rhs_t(const DevMech& m, Cta<NW>& c, const double* y, double
   Scal s;
   s.T = y[0];
   // the scalar warp: ln T and 1/T for every thread (read after the reduction's barriers)
-  double invT0 = 0.0;
   if (c.warp == Cta<NW>::SW) {
     const double lg = xlog(s.T);
-    invT0 = xrcp(s.T);
+    const double iT = xrcp(s.T);
     if (c.lane == 0) {
       c.red[SC_LOGT] = lg;
-      c.red[SC_INVT] = invT0;
+      c.red[SC_INVT] = iT;
     }
   }
   {
@@ -811,11 +832,12 @@ __device__ Scal eval_rhs_t(const DevMech& m, Cta<NW>& c, const double* y, double
     for (int k = c.tid; k < K; k += NT) part[0] += y[1 + k] * m.invW[k];
     double o[3];
     const double T = s.T;
+    // (fin runs after the reduction's first barrier: 1/T is in shared memory by then)
     c.reduce(part, warps_for<NW>(K), [&](const double (&t)[1], double (&r)[3]) {
       const double Wbar = xrcp(t[0]);
       r[0] = Wbar;
-      r[1] = p * invT0 * Wbar * (1.0 / kRc);  // rho = p Wbar / (Rc T)
-      r[2] = kRc * T * t[0] / p;              // 1 / rho
+      r[1] = p * c.red[SC_INVT] * Wbar * (1.0 / kRc);  // rho = p Wbar / (Rc T)
+      r[2] = kRc * T * t[0] / p;                       // 1 / rho
     }, o);
     s.Wbar = o[0];
     s.rho = o[1];

@@ -83,15 +83,19 @@ __global__ void k_target_stats(const int32_t* sub, const double* hf, int64_t n, 
   }
 }
 
-// Standardised BF16 features of rows [r0, r0 + rows) (or of cells rowmap[r]).
+// Standardised BF16 features of rows [r0, r0 + rows). With zmax > 0, out[r] is set
+// to 1 for a row with a standardised feature beyond +-zmax (any thread of the row may
+// store it; all store the same value; the head kernel reads and clears it).
 __global__ void k_features(const double* T, const double* p, const double* Y, int K, int64_t r0, int64_t rows,
-                           const float* norm, bf16* X) {
+                           const float* norm, bf16* X, float zmax = 0.0f, unsigned char* out = nullptr) {
   const int D = K + 2;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < rows * D; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / D;
     const int d = (int)(e - r * D);
     const double x = feature(T, p, Y, K, r0 + r, d);
-    X[e] = __float2bfloat16((float)((x - norm[d]) / norm[D + d]));
+    const float z = (float)((x - norm[d]) / norm[D + d]);
+    X[e] = __float2bfloat16(z);
+    if (zmax > 0.0f && !(fabsf(z) <= zmax)) out[r] = 1;
   }
 }
 
@@ -239,7 +243,8 @@ struct HeadP {
   float* ln_cost;
   float* ln_h0;
   float* cost;      // exp(ln_cost)
-  double* h0;       // max(exp(ln_h0), 1e-14)
+  double* h0;       // max(exp(ln_h0), 1e-14); NaN for a row flagged in out_of_range
+  unsigned char* out_of_range;  // [rows] rows with a feature beyond the range (cleared here)
   int64_t out0;     // output row offset
 };
 
@@ -291,7 +296,12 @@ __global__ void k_head(const HeadP p, int train) {
       if (p.ln_cost) p.ln_cost[q] = l0;
       if (p.ln_h0) p.ln_h0[q] = l1;
       if (p.cost) p.cost[q] = expf(fminf(l0, 80.0f));
-      if (p.h0) p.h0[q] = fmax(exp((double)l1), 1e-14);
+      bool far = false;
+      if (p.out_of_range && p.out_of_range[r]) {
+        far = true;
+        p.out_of_range[r] = 0;
+      }
+      if (p.h0) p.h0[q] = far ? __longlong_as_double(0x7ff8000000000000LL) : fmax(exp((double)l1), 1e-14);
     }
   }
   if (train) {
@@ -368,6 +378,7 @@ struct chem_mlp_s {
   bf16 *X = nullptr, *H1 = nullptr, *H2 = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
   float *Z1 = nullptr, *Z2 = nullptr, *Tb = nullptr, *part = nullptr;
   int64_t part_cap = 0;
+  unsigned char* out_of_range = nullptr;  // [kChunk] per-row range flags (kept zero between calls)
   std::string err;
 };
 
@@ -476,7 +487,8 @@ extern "C" chem_status chem_mlp_destroy(chem_mlp m) {
   if (!m) return CHEM_ERR_INVALID_ARG;
   cudaDeviceSynchronize();
   mlp_free_scratch(m);
-  for (void* p : {(void*)m->w, (void*)m->g, (void*)m->m, (void*)m->v, (void*)m->wb, (void*)m->norm, (void*)m->part})
+  for (void* p : {(void*)m->w, (void*)m->g, (void*)m->m, (void*)m->v, (void*)m->wb, (void*)m->norm, (void*)m->part,
+                  (void*)m->out_of_range})
     if (p) cudaFree(p);
   delete m;
   return CHEM_OK;
@@ -744,15 +756,22 @@ extern "C" chem_status chem_mlp_apply_gradient(chem_mlp m, const float* grad_hos
   return CHEM_OK;
 }
 
+// zmax > 0: cells with a standardised feature beyond +-zmax training standard
+// deviations get a NaN initial step (the integrator then takes its heuristic).
 static chem_status predict_into(chem_mlp m, int64_t n, const double* T, const double* p, const double* Y, float* ln_cost,
-                                float* ln_h0, float* cost, double* h0, cudaStream_t st) {
+                                float* ln_h0, float* cost, double* h0, cudaStream_t st, float zmax = 0.0f) {
   const int D = m->D;
   chem_status s = mlp_scratch(m, std::min<int64_t>(n, kChunk), false);
   if (s != CHEM_OK) return s;
+  if (zmax > 0.0f && h0 && !m->out_of_range) {
+    MLP_TRY(m, cudaMalloc(&m->out_of_range, kChunk));
+    MLP_TRY(m, cudaMemsetAsync(m->out_of_range, 0, kChunk, st));
+  }
+  if (!h0) zmax = 0.0f;
   for (int64_t r0 = 0; r0 < n; r0 += kChunk) {
     const int rows = (int)std::min<int64_t>(kChunk, n - r0);
     const int gridE = (int)std::min<int64_t>(((int64_t)rows * D + 255) / 256, 4096);
-    k_features<<<gridE, 256, 0, st>>>(T, p, Y, m->K, r0, rows, m->norm, m->X);
+    k_features<<<gridE, 256, 0, st>>>(T, p, Y, m->K, r0, rows, m->norm, m->X, zmax, m->out_of_range);
     forward(m, rows, false, st);
     HeadP hp{};
     hp.H2 = m->H2;
@@ -764,6 +783,7 @@ static chem_status predict_into(chem_mlp m, int64_t n, const double* T, const do
     hp.ln_h0 = ln_h0;
     hp.cost = cost;
     hp.h0 = h0;
+    hp.out_of_range = zmax > 0.0f ? m->out_of_range : nullptr;
     hp.out0 = r0;
     const int hw = head_warps(rows);
     k_head<<<(hw * 32 + 255) / 256, 256, 0, st>>>(hp, 0);
@@ -785,7 +805,8 @@ chem_status chem_internal_mlp_predict(chem_handle h, const double* T, const doub
   double* hh = nullptr;
   chem_status s = chem_internal_learned_buffers(h, n, &c, &hh, nullptr);
   if (s != CHEM_OK) return s;
-  s = predict_into(h->mlp, n, T, p, Y, nullptr, nullptr, c, h0 ? hh : nullptr, st);
+  s = predict_into(h->mlp, n, T, p, Y, nullptr, nullptr, c, h0 ? hh : nullptr, st,
+                   (float)h->h0_range);
   if (s != CHEM_OK) {
     h->err = h->mlp->err;
     return s;

@@ -314,3 +314,48 @@ def test_carry_over_h0(pkg):
     print("step 2 substeps heuristic", sh, "carried", sc, "RHS evaluations", 7 * sh + 2 * n, "vs", 7 * sc,
           "time %.4f vs %.4f s" % (out["heur"]["time"], out["carry"]["time"]))
     assert sc <= 1.25 * sh
+
+
+def test_h0_range_falls_back_to_heuristic(pkg):
+    """Option h0_range = z: a cell whose standardised model input has a feature beyond
+    +-z training standard deviations starts from the heuristic, the others from the
+    prediction. Per cell, the first step and the result then equal bitwise those of
+    the heuristic run (flagged cells) or of the learned run without the range check
+    (the others): each cell is integrated by one CTA, independently of the rest. The
+    flags are recomputed here from the model's normalisation; cells within 1e-4 of the
+    threshold in some feature are left out (the device takes ln in its own rounding)."""
+    n = 8192
+    m, st_tr, dt = synth.workload("c54_65k", n_cells=n, state_seed=44)
+    _, st, _ = synth.workload("c54_65k", n_cells=n, state_seed=45)
+    st = synth.perturb_states(st, seed=3)
+    heur = pkg.Integrator(m, precision=1, scheduler=2)
+    Ttr, ptr, Ytr = _dev(st_tr.T), _dev(st_tr.p), _dev(st_tr.Y)
+    sub, hf = pkg.log_cells(heur, Ttr, ptr, Ytr, dt)
+    model = pkg.CostModel(m.n_species, seed=6)
+    model.train(Ttr, ptr, Ytr, sub, hf, epochs=4, batch=8192, lr=1e-3, seed=7)
+    z = 2
+    D = m.n_species + 2
+    prm = model.get_params()
+    mu, sd = prm[:D].astype(np.float64), prm[D:2 * D].astype(np.float64)
+    x = np.concatenate([(st.T / 1000.0)[:, None], np.log(st.p)[:, None], np.log(st.Y + 1e-20)], axis=1)
+    za = np.abs(((x - mu) / sd).astype(np.float32))
+    far = (za > z).any(axis=1)
+    clear = ~(np.abs(za - z) < 1e-4).any(axis=1)
+    print("cells beyond %d sd: %d of %d (%d near the threshold)" % (z, far.sum(), n, (~clear).sum()))
+    assert 0 < far.sum() < n
+    runs = {}
+    for name, opts in (("heur", {}), ("learned", {"h0": 1}), ("ranged", {"h0": 1, "h0_range": z})):
+        integ = pkg.Integrator(m, precision=1, scheduler=2, **opts)
+        if opts:
+            model.attach(integ)
+        T, p, Y = _dev(st.T), _dev(st.p), _dev(st.Y)
+        integ.integrate(T, p, Y, dt, RTOL, ATOL)
+        s = integ.stats(n)
+        assert int((s["status"] != 0).sum()) == 0, name
+        runs[name] = (s["h_first"].cpu().numpy(), T.cpu().numpy(), Y.cpu().numpy())
+    for i, name in ((0, "h_first"), (1, "T"), (2, "Y")):
+        r = runs["ranged"][i]
+        np.testing.assert_array_equal(r[far & clear], runs["heur"][i][far & clear], err_msg=name)
+        np.testing.assert_array_equal(r[~far & clear], runs["learned"][i][~far & clear], err_msg=name)
+    # the learned prediction does differ from the heuristic (the test would be vacuous otherwise)
+    assert np.any(runs["learned"][0][far & clear] != runs["heur"][0][far & clear])
