@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--no-h0-guard", action="store_true",
                     help="with --cfd-loop: the learned initial step as predicted, without the starting-step "
                          "envelope check (option h0_guard = 0)")
-    ap.add_argument("--h0-range", type=int, default=0,
+    ap.add_argument("--h0-range", type=int, default=10,
                     help="with --cfd-loop: option h0_range (cells with a standardised model input beyond "
                          "this many training standard deviations start from the heuristic; 0 = off)")
     ap.add_argument("--diag-h0", action="store_true",

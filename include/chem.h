@@ -219,7 +219,8 @@ chem_status chem_integrate_jobs(const chem_job* jobs, int32_t n_jobs, double dt,
  *   "h0_range"    with h0 = 1: z > 0 = a cell whose standardised model input has a
  *                 feature beyond +-z standard deviations of the training data
  *                 starts from the heuristic instead of the prediction (the model is
- *                 not trusted outside the states it was trained on); 0 (default) = off
+ *                 not trusted outside the states it was trained on; default 10);
+ *                 0 = off
  *   "max_steps"   step budget per cell (default 100000)
  *   "block"       threads per cell: 64, 128 or 256; 0 (default) = the size with
  *                 the most resident warps per SM for the mechanism and precision
@@ -396,8 +397,12 @@ chem_status chem_lu_solve_batched(int64_t n_mat, int32_t dim, const double* A, c
  * functions the rate kernels use: op 0 exp (Tang's table-driven method), op 1 ln
  * (table-driven, Tang's manner), op 2 1/x (Newton's iteration on the hardware's
  * approximate reciprocal); arguments outside their reduced ranges (see the kernel
- * source) follow the CUDA library routine or the IEEE division. Returns
- * CHEM_ERR_INVALID_ARG for an unknown op, n < 0 or NULL arrays with n > 0.
+ * source) follow the CUDA library routine or the IEEE division. Ops 3 and 4 return
+ * the hi and lo parts (widened to double) of the split of x into a float-float pair
+ * that the mixed form's Jacobian assembly and refinement use: hi = x truncated to 24
+ * significant bits, lo = x - hi rounded to FP32; |x| < 2^-126 gives (0, 0), |x| >=
+ * 2^128 gives (+-inf, 0). Returns CHEM_ERR_INVALID_ARG for an unknown op, n < 0 or
+ * NULL arrays with n > 0.
  */
 chem_status chem_eval_math(int32_t op, int64_t n, const double* x, double* y, void* stream);
 

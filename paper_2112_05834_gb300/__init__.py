@@ -315,10 +315,11 @@ def lu_solve_batched(A, b, precision=0, ir_sweeps=2, stream=None):
 
 def eval_math(op, x, stream=None):
     """Elementwise exp ("exp"), ln ("log") or 1/x ("rcp") of a CUDA float64 tensor by
-    the rate kernels' own routines."""
+    the rate kernels' own routines; "ff_hi" / "ff_lo": the parts of the float-float
+    split the mixed form's assembly and refinement use."""
     import torch
 
-    code = {"exp": 0, "log": 1, "rcp": 2}[op]
+    code = {"exp": 0, "log": 1, "rcp": 2, "ff_hi": 3, "ff_lo": 4}[op]
     xc = x.contiguous()
     y = torch.empty_like(xc)
     _check(load().chem_eval_math(code, xc.numel(), _dptr(xc), _dptr(y), _stream_ptr(stream)))

@@ -474,12 +474,19 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
   for (size_t e = 0; e < sp_ent.size(); ++e) sp_nu[e] = sp_ent[e].y;
   for (int k = 0; k < K; ++k)
     for (int e = tr_ptr[k]; e < tr_ptr[k + 1]; ++e) tr_nu[e] = tr_ent[e].y * d->W[k];
-  std::vector<float> eff_ff(2 * eff.size());
-  for (size_t e = 0; e < eff.size(); ++e) {
-    const float h = (float)eff[e];
-    eff_ff[2 * e] = h;
-    eff_ff[2 * e + 1] = (float)(eff[e] - (double)h);
-  }
+  // float-float (hi, lo) copies of the constants the mixed form's assembly multiplies by
+  auto split = [](const std::vector<double>& v) {
+    std::vector<float> o(2 * v.size());
+    for (size_t e = 0; e < v.size(); ++e) {
+      const float h = (float)v[e];
+      o[2 * e] = h;
+      o[2 * e + 1] = (float)(v[e] - (double)h);
+    }
+    return o;
+  };
+  const std::vector<float> eff_ff = split(eff), invW_ff = split(invW), tr_nu_ff = split(tr_nu);
+  std::vector<float> js_nu_ff[3];
+  for (int v = 0; v < 3; ++v) js_nu_ff[v] = split(js_nu[v]);
   Pool P;
   const size_t oW = P.add(W.data(), W.size() * 8), oiW = P.add(invW.data(), invW.size() * 8),
                oN = P.add(nasa.data(), nasa.size() * 8), oA = P.add(arr.data(), arr.size() * 8),
@@ -489,12 +496,14 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
                oTp = P.add(tr_ptr.data(), tr_ptr.size() * 4), oTe = P.add(tr_ent.data(), tr_ent.size() * 8),
                oSn = P.add(sp_nu.data(), sp_nu.size() * 8), oTn = P.add(tr_nu.data(), tr_nu.size() * 8),
                oJm = P.add(jmask.data(), jmask.size() * 4),
-               oEf = P.add(eff_ff.data(), eff_ff.size() * 4);
-  size_t oJe[3], oJn[3], oCs[3];
+               oEf = P.add(eff_ff.data(), eff_ff.size() * 4), oiWf = P.add(invW_ff.data(), invW_ff.size() * 4),
+               oTnf = P.add(tr_nu_ff.data(), tr_nu_ff.size() * 4);
+  size_t oJe[3], oJn[3], oJnf[3], oCs[3];
   for (int v = 0; v < 3; ++v) {
     oCs[v] = P.add(chunk_sched[v].data(), chunk_sched[v].size() * 4);
     oJe[v] = P.add(js_ent[v].data(), js_ent[v].size() * sizeof(int2));
     oJn[v] = P.add(js_nu[v].data(), js_nu[v].size() * 8);
+    oJnf[v] = P.add(js_nu_ff[v].data(), js_nu_ff[v].size() * 4);
   }
   CHEM_CUDA(h, cudaMalloc(&h->d_tables, P.host.size()));
   CHEM_CUDA(h, cudaMemcpy(h->d_tables, P.host.data(), P.host.size(), cudaMemcpyHostToDevice));
@@ -525,10 +534,13 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
   m.sp_nu = reinterpret_cast<const double*>(b + oSn);
   m.tr_nu = reinterpret_cast<const double*>(b + oTn);
   m.eff_ff = reinterpret_cast<const chem::ff2*>(b + oEf);
+  m.invW_ff = reinterpret_cast<const chem::ff2*>(b + oiWf);
+  m.tr_nu_ff = reinterpret_cast<const chem::ff2*>(b + oTnf);
   m.jmask = reinterpret_cast<const unsigned*>(b + oJm);
   for (int v = 0; v < 3; ++v) {
     m.js_ent[v] = reinterpret_cast<const int2*>(b + oJe[v]);
     m.js_nu[v] = reinterpret_cast<const double*>(b + oJn[v]);
+    m.js_nu_ff[v] = reinterpret_cast<const chem::ff2*>(b + oJnf[v]);
     m.js_rounds[v] = js_rounds[v];
     m.chunk_sched[v] = reinterpret_cast<const int*>(b + oCs[v]);
   }
@@ -1154,7 +1166,7 @@ extern "C" chem_status chem_lu_solve_batched(int64_t n_mat, int32_t dim, const d
 }
 
 extern "C" chem_status chem_eval_math(int32_t op, int64_t n, const double* x, double* y, void* stream) {
-  if (op < 0 || op > 2 || n < 0 || (n > 0 && (!x || !y))) return CHEM_ERR_INVALID_ARG;
+  if (op < 0 || op > 4 || n < 0 || (n > 0 && (!x || !y))) return CHEM_ERR_INVALID_ARG;
   return launch_math(op, x, y, n, static_cast<cudaStream_t>(stream)) == cudaSuccess ? CHEM_OK : CHEM_ERR_CUDA;
 }
 

@@ -45,7 +45,7 @@ struct chem_handle_s {
   int job_launch = 0;                     // option "job_launch": 1 = one launch per job, concurrent streams
   int method = 0;                         // option "method": 0 = RODAS4, 1 = ROS34PW2 (W-method)
   int h0_guard = 1;                       // option "h0_guard": envelope check of supplied initial steps
-  int h0_range = 0;                       // option "h0_range": learned h0 only within +-h0_range sd (0: off)
+  int h0_range = 10;                      // option "h0_range": learned h0 only within +-h0_range sd (0: off)
   cudaStream_t side = nullptr;            // the handle's stream for concurrent jobs
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t kev0 = nullptr, kev1 = nullptr;

@@ -38,37 +38,112 @@ namespace chem {
 #define FULLMASK 0xffffffffu
 
 // ---------------------------------------------------------------------------
-// Float-float arithmetic (a value is hi + lo with two FP32 numbers): error-free
-// products with FMA (Dekker/Ogita-Rump-Oishi style TwoProduct) and TwoSum
-// (Knuth) give about 44-48 significant bits on the FP32 pipe, which on GB300
-// runs ~60x faster than the FP64 pipe. Used by the mixed form for long sums of
-// products (third-body concentrations, refinement residuals).
+// Float-float arithmetic (a value is hi + lo with two FP32 numbers, |lo| <= ulp(hi)/2):
+// error-free products with FMA (Dekker's TwoProduct) and sums by Knuth's TwoSum
+// give about 44-48 significant bits on the FP32 pipe. On GB300 an SM's FP32 pipe
+// completes 64 times the operations per clock of its FP64 pipe, which the
+// integration keeps busy, so the mixed form runs its long sums of products here:
+// third-body concentrations, the Jacobian assembly and the refinement residuals.
+// The _rn intrinsics keep the compiler from contracting a product and a sum into
+// one FMA, which would break the error-free transformations.
 // ---------------------------------------------------------------------------
-struct ff2 {
+struct __align__(8) ff2 {
   float hi, lo;
 };
+// Conversions between FP64 and FP32 run on the FP64 pipe on this part, at its rate,
+// so the splits and widenings below use integer operations on the bit patterns.
+// Double to float-float: hi = x truncated to 24 significant bits, lo = x - hi (the
+// 29 remaining mantissa bits, rounded to 24 by the integer-to-float conversion and
+// scaled by an exact power of two). In FP32's subnormal range (2^-149 <= |x| <
+// 2^-126) hi = x truncated to a multiple of 2^-149 and lo = 0; below it (0, 0);
+// |x| >= 2^128 gives +-inf (NaN stays NaN) with lo = 0.
 __device__ __forceinline__ ff2 ff_split(double x) {
-  const float h = (float)x;
-  return {h, (float)(x - (double)h)};
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+  const unsigned sgn = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7FFu);
+  const float m = __uint2float_rn(lw & 0x1FFFFFFFu);
+  // m 2^(e - 1075) as one power-of-two factor for e >= 949, else as 2^(e - 1011) 2^-64
+  const bool big = e >= 949;
+  const float s1 = __uint_as_float((unsigned)(big ? e - 948 : e - 884) << 23);
+  const float s2 = big ? 1.0f : __uint_as_float(0x1F800000u);  // 2^-64
+  ff2 r = {__uint_as_float(sgn | ((unsigned)(e - 896) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29)),
+           __uint_as_float(__float_as_uint(__fmul_rn(__fmul_rn(m, s1), s2)) | sgn)};
+  if (e < 897) {
+    const int sh = 926 - e;  // the 53-bit significand times 2^(e - 1075) in units of 2^-149
+    const unsigned frac = sh <= 52 ? (unsigned)(((1ull << 52) | (b & 0xFFFFFFFFFFFFFull)) >> sh) : 0u;
+    r = {__uint_as_float(sgn | frac), 0.0f};
+  }
+  if (e > 1150) {
+    const bool nan = e == 2047 && ((hw & 0xFFFFFu) | lw) != 0u;
+    r = {__uint_as_float(sgn | 0x7F800000u | (nan ? 0x400000u : 0u)), 0.0f};
+  }
+  return r;
 }
-__device__ __forceinline__ double ff_value(ff2 a) { return (double)a.hi + (double)a.lo; }
-// s + p (both float-float), renormalised
+// float to double, exactly
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu, mant = u & 0x7FFFFFu, sgn = u & 0x80000000u;
+  unsigned hw = sgn | ((e + 896u) << 20) | (mant >> 3), lw = mant << 29;
+  if (e == 0u) {
+    // zero or subnormal mant 2^-149 = 2^(p - 149) (1 + f), p = position of the leading bit
+    const int p = 31 - __clz(mant);
+    const unsigned long long fr = (unsigned long long)mant << (52 - p);
+    hw = mant ? sgn | ((unsigned)(p + 874) << 20) | ((unsigned)(fr >> 32) & 0xFFFFFu) : sgn;
+    lw = mant ? (unsigned)fr : 0u;
+  } else if (e == 255u) {
+    hw = sgn | 0x7FF00000u | (mant >> 3) | (mant ? 0x80000u : 0u);
+    lw = 0u;
+  }
+  return __hiloint2double((int)hw, (int)lw);
+}
+__device__ __forceinline__ double ff_value(ff2 a) { return f32_to_f64(a.hi) + f32_to_f64(a.lo); }
+__device__ __forceinline__ ff2 ff_neg(ff2 a) { return {-a.hi, -a.lo}; }
+// s + e renormalised, |s| >= |e| (or s == 0)
+__device__ __forceinline__ ff2 fast_two_sum(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+// a + b = s + e exactly (Knuth)
+__device__ __forceinline__ ff2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
 __device__ __forceinline__ ff2 ff_add(ff2 a, ff2 b) {
-  const float s = a.hi + b.hi;
-  const float bb = s - a.hi;
-  float e = (a.hi - (s - bb)) + (b.hi - bb);
-  e += a.lo + b.lo;
-  const float h = s + e;
-  return {h, e - (h - s)};
+  const ff2 s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
-// a * b (both float-float); the lo * lo term is below the precision kept
-__device__ __forceinline__ ff2 ff_mul(ff2 a, ff2 b) {
-  const float p = a.hi * b.hi;
+__device__ __forceinline__ ff2 ff_sub(ff2 a, ff2 b) { return ff_add(a, ff_neg(b)); }
+// hi * hi exactly, plus the cross terms (the lo * lo term is below the precision kept)
+__device__ __forceinline__ ff2 ff_prod(ff2 a, ff2 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
   float e = fmaf(a.hi, b.hi, -p);
   e = fmaf(a.hi, b.lo, e);
   e = fmaf(a.lo, b.hi, e);
-  const float h = p + e;
-  return {h, e - (h - p)};
+  return {p, e};  // not renormalised
+}
+__device__ __forceinline__ ff2 ff_mul(ff2 a, ff2 b) {
+  const ff2 p = ff_prod(a, b);
+  return fast_two_sum(p.hi, p.lo);
+}
+// a * b + c
+__device__ __forceinline__ ff2 ff_fma(ff2 a, ff2 b, ff2 c) {
+  const ff2 p = ff_prod(a, b);
+  const ff2 s = two_sum(p.hi, c.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(p.lo, c.lo)));
+}
+// conversions between the matrix element types (double, float, float-float)
+__device__ __forceinline__ float to_float(float a) { return a; }
+__device__ __forceinline__ float to_float(double a) { return (float)a; }
+__device__ __forceinline__ float to_float(ff2 a) { return a.hi; }
+__device__ __forceinline__ double to_double(float a) { return (double)a; }
+__device__ __forceinline__ double to_double(double a) { return a; }
+__device__ __forceinline__ double to_double(ff2 a) { return ff_value(a); }
+template <class R>
+__device__ __forceinline__ R from_double(double a) {
+  if constexpr (std::is_same<R, ff2>::value) return ff_split(a);
+  else return (R)a;
 }
 
 // ---------------------------------------------------------------------------
@@ -587,7 +662,7 @@ struct Policy {
 template <>
 struct Policy<PREC_MIXED> {
   using LU = float;
-  using ASM = double;
+  using ASM = ff2;  // float-float: about 48 significant bits, on the FP32 pipe
   static constexpr bool IR = true;
 };
 template <>
@@ -923,7 +998,7 @@ __device__ Scal eval_rhs_t(const DevMech& m, Cta<NW>& c, const double* y, double
         const ff2* ef = m.eff_ff + (size_t)(i - m.i_tb0) * K;
         const ff2* Cf = reinterpret_cast<const ff2*>(c.dk);
         ff2 acc = {0.0f, 0.0f};
-        for (int k = 0; k < K; ++k) acc = ff_add(acc, ff_mul(ef[k], Cf[k]));
+        for (int k = 0; k < K; ++k) acc = ff_fma(ef[k], Cf[k], acc);
         Mc = ff_value(acc);
       } else {
         for (int k = 0; k < K; ++k) Mc += e[k] * c.C[k];
@@ -1000,11 +1075,22 @@ __device__ Scal eval_rhs_t(const DevMech& m, Cta<NW>& c, const double* y, double
       double dH = c.hRT[sl.z] + (sl.w >= 0 ? c.hRT[sl.w] : 0.0) - c.hRT[sl.x] -
                   (sl.y >= 0 ? c.hRT[sl.y] : 0.0);
       const double dlnKc = (dH - ar.w) * invT;
-      double* dq = c.dqs + 4 * i;
+      double dq[4];
       dq[0] = phi * kf * Cb;
       dq[1] = sl.y >= 0 ? phi * kf * Ca : 0.0;
       dq[2] = -phi * kr * Cd;
       dq[3] = sl.w >= 0 ? -phi * kr * Cc : 0.0;
+      if (FF) {
+        // the float-float assembly's copy (hi, lo), split once here
+        ff2* dqf = reinterpret_cast<ff2*>(c.dqs) + 4 * i;
+        dqf[0] = ff_split(dq[0]);
+        dqf[1] = sl.y >= 0 ? ff_split(dq[1]) : ff2{0.0f, 0.0f};
+        dqf[2] = ff_split(dq[2]);
+        dqf[3] = sl.w >= 0 ? ff_split(dq[3]) : ff2{0.0f, 0.0f};
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) c.dqs[4 * i + u] = dq[u];
+      }
       double Dsum = Ca * dq[0] + (sl.y >= 0 ? Cb * dq[1] : 0.0) + Cc * dq[2] + (sl.w >= 0 ? Cd * dq[3] : 0.0);
       double dtc, Pc;
       if (i >= m.i_fo0) {
@@ -1019,7 +1105,10 @@ __device__ Scal eval_rhs_t(const DevMech& m, Cta<NW>& c, const double* y, double
       }
       if (i >= m.i_tb0) Dsum += Mc * Pc;
       c.dTc[i] = dtc;
-      c.P[i] = Pc;
+      if (FF)
+        reinterpret_cast<ff2*>(c.P)[i] = ff_split(Pc);
+      else
+        c.P[i] = Pc;
       c.D[i] = Dsum;
     }
   }
@@ -1112,7 +1201,15 @@ __device__ __forceinline__ R fmaR(R a, R b, R c) {
   else return fma(a, b, c);
 }
 
-template <int NW, class R, bool JO, int U>
+// FFD: the per-reaction data (dq/dC, P) is stored as float-float pairs (the forms
+// with FP32 factors); R = float then reads their hi parts.
+template <bool FFD>
+__device__ __forceinline__ double rx_data(const double* a, int i) {
+  if constexpr (FFD) return (double)reinterpret_cast<const ff2*>(a)[i].hi;
+  else return a[i];
+}
+
+template <int NW, class R, bool JO, int U, bool FFD>
 __device__ void assemble_rows(const DevMech& m, Cta<NW>& c, R* A, int K, int ld, R rf) {
   constexpr double SG = JO ? 1.0 : -1.0;
   for (int k = c.warp; k < K; k += NW) {
@@ -1133,7 +1230,7 @@ __device__ void assemble_rows(const DevMech& m, Cta<NW>& c, R* A, int K, int ld,
       int rl = 0;
       if (t < t1) {
         const int ri = m.tr_ent[t].x;
-        cl = R(SG * m.tr_nu[t] * c.P[ri]);
+        cl = R(SG * m.tr_nu[t] * rx_data<FFD>(c.P, ri));
         rl = ri - m.i_tb0;
       }
       const int cnt = min(32, t1 - tb);
@@ -1155,7 +1252,7 @@ __device__ void assemble_rows(const DevMech& m, Cta<NW>& c, R* A, int K, int ld,
   }
 }
 
-template <int NW, class R, bool JO>
+template <int NW, class R, bool JO, bool FFD = false>
 __device__ void assemble(const DevMech& m, Cta<NW>& c, const Scal& s, const double* f, double fac, void* target) {
   constexpr int NT = NW * 32;
   constexpr double SG = JO ? 1.0 : -1.0;
@@ -1178,7 +1275,7 @@ __device__ void assemble(const DevMech& m, Cta<NW>& c, const Scal& s, const doub
     R a = R(0);
     for (int r = 0; r < rounds; ++r) {
       const int2 e = se[r * NT];
-      if (e.x >= 0) a = fmaR(R(SG * sn[r * NT]), R(c.dqs[e.x]), a);
+      if (e.x >= 0) a = fmaR(R(SG * sn[r * NT]), R(rx_data<FFD>(c.dqs, e.x)), a);
       if (e.y >= 0) {
         A[e.y] = a;
         a = R(0);
@@ -1188,14 +1285,14 @@ __device__ void assemble(const DevMech& m, Cta<NW>& c, const Scal& s, const doub
   __syncthreads();
   // (2) species rows
   switch ((K + 31) >> 5) {
-    case 1: assemble_rows<NW, R, JO, 1>(m, c, A, K, ld, rf); break;
-    case 2: assemble_rows<NW, R, JO, 2>(m, c, A, K, ld, rf); break;
-    case 3: assemble_rows<NW, R, JO, 3>(m, c, A, K, ld, rf); break;
-    case 4: assemble_rows<NW, R, JO, 4>(m, c, A, K, ld, rf); break;
-    case 5: assemble_rows<NW, R, JO, 5>(m, c, A, K, ld, rf); break;
-    case 6: assemble_rows<NW, R, JO, 6>(m, c, A, K, ld, rf); break;
-    case 7: assemble_rows<NW, R, JO, 7>(m, c, A, K, ld, rf); break;
-    default: assemble_rows<NW, R, JO, 8>(m, c, A, K, ld, rf); break;
+    case 1: assemble_rows<NW, R, JO, 1, FFD>(m, c, A, K, ld, rf); break;
+    case 2: assemble_rows<NW, R, JO, 2, FFD>(m, c, A, K, ld, rf); break;
+    case 3: assemble_rows<NW, R, JO, 3, FFD>(m, c, A, K, ld, rf); break;
+    case 4: assemble_rows<NW, R, JO, 4, FFD>(m, c, A, K, ld, rf); break;
+    case 5: assemble_rows<NW, R, JO, 5, FFD>(m, c, A, K, ld, rf); break;
+    case 6: assemble_rows<NW, R, JO, 6, FFD>(m, c, A, K, ld, rf); break;
+    case 7: assemble_rows<NW, R, JO, 7, FFD>(m, c, A, K, ld, rf); break;
+    default: assemble_rows<NW, R, JO, 8, FFD>(m, c, A, K, ld, rf); break;
   }
   __syncthreads();
   // (3) temperature row; with acc = sum_k e_k S_kj, sum_k e_k J_kj = sg (acc - rf e_(j-1)),
@@ -1209,6 +1306,121 @@ __device__ void assemble(const DevMech& m, Cta<NW>& c, const Scal& s, const doub
       v = rf - acc - R(SG * (s.Scpw * s.irho * s.icpm + ft * s.dcpm));
     else
       v = rf * R(c.ek[j - 1]) - acc - R(SG * ft * c.cpR[j - 1] * kRc * m.invW[j - 1]);
+    A[j] = v;
+  }
+  __syncthreads();
+}
+
+// The same assembly in float-float arithmetic (the mixed form): the same terms in the
+// same order, from float-float copies of the per-reaction data (dq/dC and P, split
+// once by eval_rhs) and of the mechanism's constants (1/W, nu W, efficiencies), so
+// that every sum and product of the pass runs on the FP32 pipe; the species-level
+// scalars are formed in FP64 and split once per species. A holds (hi, lo) per entry;
+// its error is a few units of 2^-48 relative to the sums' terms, far below the FP32
+// factorisation's, so the refinement converges to the same solutions.
+template <int NW, bool JO, int U>
+__device__ void assemble_rows_ff(const DevMech& m, Cta<NW>& c, ff2* A, int K, int ld, ff2 rf) {
+  const ff2* beta_ff = reinterpret_cast<const ff2*>(c.akT);
+  const ff2* Pf = reinterpret_cast<const ff2*>(c.P);
+  const ff2 zero = {0.0f, 0.0f};
+  for (int k = c.warp; k < K; k += NW) {
+    ff2* row = A + (1 + k) * ld + 1;
+    const ff2 beta = beta_ff[k];
+    ff2 acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const unsigned msk = m.jmask[k * U + u];
+      acc[u] = ((msk >> c.lane) & 1u) ? ff_add(beta, row[c.lane + 32 * u]) : beta;
+    }
+    const int t1 = m.tr_ptr[k + 1];
+    for (int tb = m.tr_ptr[k]; tb < t1; tb += 32) {
+      const int t = tb + c.lane;
+      ff2 cl = zero;
+      int rl = 0;
+      if (t < t1) {
+        const int ri = m.tr_ent[t].x;
+        const ff2 tn = m.tr_nu_ff[t];
+        cl = ff_mul(JO ? tn : ff_neg(tn), Pf[ri]);
+        rl = ri - m.i_tb0;
+      }
+      const int cnt = min(32, t1 - tb);
+      for (int q = 0; q < cnt; ++q) {
+        const ff2 coef = {__shfl_sync(FULLMASK, cl.hi, q), __shfl_sync(FULLMASK, cl.lo, q)};
+        const ff2* e = m.eff_ff + (size_t)__shfl_sync(FULLMASK, rl, q) * K;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int j = c.lane + 32 * u;
+          if (u < U - 1 || j < K) acc[u] = ff_fma(coef, e[j], acc[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = c.lane + 32 * u;
+      if (u < U - 1 || j < K) row[j] = ff_fma(acc[u], m.invW_ff[j], j == k ? rf : zero);
+    }
+  }
+}
+
+template <int NW, bool JO>
+__device__ void assemble_ff(const DevMech& m, Cta<NW>& c, const Scal& s, const double* f, double fac, ff2* A) {
+  constexpr int NT = NW * 32;
+  constexpr double SG = JO ? 1.0 : -1.0;
+  const int K = m.K, n = K + 1, ld = odd_ld(n);
+  const ff2 zero = {0.0f, 0.0f};
+  const ff2 rf = JO ? zero : ff_split(fac);
+  ff2* ek = reinterpret_cast<ff2*>(c.ek);
+  ff2* beta = reinterpret_cast<ff2*>(c.akT);
+  const ff2* dq = reinterpret_cast<const ff2*>(c.dqs);
+  // (1) species pass
+  const double eT = kRc * s.T * s.icpm, wr = s.Wbar * s.irho;
+  for (int k = c.tid; k < K; k += NT) {
+    ek[k] = ff_split(c.hRT[k] * eT * m.invW[k]);
+    const double Wk = m.W[k], dk = c.dk[k], fk = f[1 + k];
+    A[(1 + k) * ld] = ff_split(SG * (Wk * s.irho * (c.akT[k] - dk * s.invT) + fk * s.invT));
+    beta[k] = ff_split(SG * (fk * s.Wbar - Wk * wr * dk));  // beta_k (a_kT is consumed)
+  }
+  {
+    const int v = NT == 64 ? 0 : NT == 128 ? 1 : 2;
+    const int2* se = m.js_ent[v] + c.tid;
+    const ff2* sn = m.js_nu_ff[v] + c.tid;
+    const int rounds = m.js_rounds[v];
+    ff2 a = zero;
+    for (int r = 0; r < rounds; ++r) {
+      const int2 e = se[r * NT];
+      if (e.x >= 0) {
+        const ff2 w = sn[r * NT];
+        a = ff_fma(JO ? w : ff_neg(w), dq[e.x], a);
+      }
+      if (e.y >= 0) {
+        A[e.y] = a;
+        a = zero;
+      }
+    }
+  }
+  __syncthreads();
+  // (2) species rows
+  switch ((K + 31) >> 5) {
+    case 1: assemble_rows_ff<NW, JO, 1>(m, c, A, K, ld, rf); break;
+    case 2: assemble_rows_ff<NW, JO, 2>(m, c, A, K, ld, rf); break;
+    case 3: assemble_rows_ff<NW, JO, 3>(m, c, A, K, ld, rf); break;
+    case 4: assemble_rows_ff<NW, JO, 4>(m, c, A, K, ld, rf); break;
+    case 5: assemble_rows_ff<NW, JO, 5>(m, c, A, K, ld, rf); break;
+    case 6: assemble_rows_ff<NW, JO, 6>(m, c, A, K, ld, rf); break;
+    case 7: assemble_rows_ff<NW, JO, 7>(m, c, A, K, ld, rf); break;
+    default: assemble_rows_ff<NW, JO, 8>(m, c, A, K, ld, rf); break;
+  }
+  __syncthreads();
+  // (3) temperature row, as in assemble()
+  const double ft = s.fT * s.icpm;
+  for (int j = NT - 1 - c.tid; j < n; j += NT) {
+    ff2 acc = zero;
+    for (int k = 0; k < K; ++k) acc = ff_fma(ek[k], A[(1 + k) * ld + j], acc);
+    ff2 v;
+    if (j == 0)
+      v = ff_sub(ff_sub(rf, acc), ff_split(SG * (s.Scpw * s.irho * s.icpm + ft * s.dcpm)));
+    else
+      v = ff_sub(ff_sub(ff_mul(rf, ek[j - 1]), acc), ff_split(SG * ft * c.cpR[j - 1] * kRc * m.invW[j - 1]));
     A[j] = v;
   }
   __syncthreads();
@@ -1583,33 +1795,59 @@ __device__ void solve(Cta<NW>& c, int n, const double* b, double* x, int ir) {
     if (c.warp == Cta<NW>::SW) lu_solve_warp<double>(reinterpret_cast<double*>(c.M), n, c.invd, x, c.lane);
     __syncthreads();
   } else {
+    using A = typename P::ASM;
     const float* Ai = reinterpret_cast<const float*>(c.M);
-    const typename P::ASM* M0 = reinterpret_cast<const typename P::ASM*>(c.M0);
+    const A* M0 = reinterpret_cast<const A*>(c.M0);
     float* xf = reinterpret_cast<float*>(c.sc);  // scratch vector reused as float
+    ff2* xq = reinterpret_cast<ff2*>(c.rr);      // x as float-float pairs (rr is free in the solves)
     const int ld = odd_ld(n);
-    for (int i = c.tid; i < n; i += NT) xf[i] = (float)b[i];
+    for (int i = c.tid; i < n; i += NT) xf[i] = ff_split(b[i]).hi;
     __syncthreads();
     for (int i = c.tid; i < n; i += NT) {
       float acc = 0.0f;
       const float* row = Ai + i * ld;
       for (int j = 0; j < n; ++j) acc = fmaf(row[j], xf[j], acc);
-      x[i] = (double)acc;
+      x[i] = f32_to_f64(acc);
+      xq[i] = {acc, 0.0f};
     }
     __syncthreads();
     for (int sweep = 0; sweep < ir; ++sweep) {
-      // FP64 residual rows from the last warp down (the first warps carry the species loops)
+      // Residual rows r = b - M0 x from the last warp down (the first warps carry the
+      // species loops), as a compensated dot product on the FP32 pipe (Ogita, Rump and
+      // Oishi's Dot2: exact products of the hi parts, TwoSum of the running sum, the
+      // rounding errors and cross terms gathered in a second accumulator): as accurate as
+      // a sum in about 48-bit arithmetic, then rounded to FP32 for the correction solve.
       for (int i = NT - 1 - c.tid; i < n; i += NT) {
-        double acc = b[i];
-        const typename P::ASM* row = M0 + i * ld;
-        for (int j = 0; j < n; ++j) acc -= (double)row[j] * x[j];
-        xf[i] = (float)acc;
+        const ff2 bi = ff_split(b[i]);
+        float sh = bi.hi, sl = bi.lo;
+        const A* row = M0 + i * ld;
+        for (int j = 0; j < n; ++j) {
+          const ff2 xj = xq[j];
+          float mh, ml = 0.0f;
+          if constexpr (std::is_same<A, ff2>::value) {
+            const ff2 mj = row[j];
+            mh = mj.hi;
+            ml = mj.lo;
+          } else {
+            mh = row[j];
+          }
+          const float p = __fmul_rn(mh, xj.hi);
+          float pe = fmaf(mh, xj.hi, -p);
+          pe = fmaf(mh, xj.lo, pe);
+          if constexpr (std::is_same<A, ff2>::value) pe = fmaf(ml, xj.hi, pe);
+          const ff2 t = two_sum(sh, -p);
+          sh = t.hi;
+          sl = __fadd_rn(sl, __fsub_rn(t.lo, pe));
+        }
+        xf[i] = __fadd_rn(sh, sl);
       }
       __syncthreads();
       for (int i = c.tid; i < n; i += NT) {
         float acc = 0.0f;
         const float* row = Ai + i * ld;
         for (int j = 0; j < n; ++j) acc = fmaf(row[j], xf[j], acc);
-        x[i] += (double)acc;
+        x[i] += f32_to_f64(acc);
+        if (sweep + 1 < ir) xq[i] = ff_split(x[i]);
       }
       __syncthreads();
     }
@@ -1644,13 +1882,16 @@ __device__ void build_matrix(const DevMech& m, Cta<NW>& c, const Scal& s, const 
   if constexpr (!P::IR) {
     assemble<NW, double, JO>(m, c, s, f, fac, c.M);
   } else {
-    assemble<NW, typename P::ASM, JO>(m, c, s, f, fac, c.M0);
+    if constexpr (std::is_same<typename P::ASM, ff2>::value)
+      assemble_ff<NW, JO>(m, c, s, f, fac, reinterpret_cast<ff2*>(c.M0));
+    else
+      assemble<NW, typename P::ASM, JO, true>(m, c, s, f, fac, c.M0);
     if (JO) return;
     const int n = m.K + 1, ld = odd_ld(n);
     const typename P::ASM* src = reinterpret_cast<const typename P::ASM*>(c.M0);
     float* dst = reinterpret_cast<float*>(c.M);
     for (int i = c.warp; i < n; i += NW)
-      for (int j = c.lane; j < n; j += 32) dst[i * ld + j] = (float)src[i * ld + j];
+      for (int j = c.lane; j < n; j += 32) dst[i * ld + j] = to_float(src[i * ld + j]);
     __syncthreads();
   }
 }

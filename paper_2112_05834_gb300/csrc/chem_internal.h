@@ -59,6 +59,7 @@ struct DevMech {
   double T_bigG;  // below this T some species may have |G/RT| > kBigGRT (0: never in [kTmin, kTmax])
   const double* W;      // [K]
   const double* invW;   // [K]
+  const struct ff2* invW_ff;  // [K] as float-float pairs (hi, lo)
   const double* nasa;   // [K][36]: for range r (0 below T_mid, 1 above) at 17 r:
                         //   cp/R coefficients a1..a5, H/RT coefficients a1, a2/2, a3/3,
                         //   a4/4, a5/5, a6, S/R coefficients a1, a2, a3/2, a4/3, a5/4, a7;
@@ -81,9 +82,11 @@ struct DevMech {
   // matrix offset the finished sum goes to (-1: the pair continues).
   const int2* js_ent[3];
   const double* js_nu[3];  // nu_ki W_k of the term
+  const struct ff2* js_nu_ff[3];  // the same as float-float pairs
   int js_rounds[3];
   const unsigned* jmask;   // [K][ceil(K/32)]: bit l of word (k, u) set if pair (k, l + 32 u) exists
   const double* tr_nu;  // nu_ki W_k of the tr_ent entries
+  const struct ff2* tr_nu_ff;  // the same as float-float pairs
   const int* tr_ptr;    // [K+1] row k -> (reaction i with [M], nu_ki)
   const int2* tr_ent;
 };

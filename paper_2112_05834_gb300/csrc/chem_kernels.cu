@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(NW * 32) k_diag(const __grid_constant__ DiagAr
       }
       const A* J = reinterpret_cast<const A*>(Policy<PREC>::IR ? c.M0 : c.M);
       for (int i = c.warp; i < n; i += NW)
-        for (int j = c.lane; j < n; j += 32) a.out[(size_t)cell * n * n + i * n + j] = (double)J[i * ld + j];
+        for (int j = c.lane; j < n; j += 32) a.out[(size_t)cell * n * n + i * n + j] = to_double(J[i * ld + j]);
     } else {
       eval_rhs<NW, false, Policy<PREC>::IR>(a.m, c, c.y, p, c.f0);
       const double h = starting_step<NW, Policy<PREC>::IR>(a.m, c, p, a.dt, a.rtol, a.atol, a.q);
@@ -62,10 +62,17 @@ __global__ void __launch_bounds__(NW * 32) k_diag(const __grid_constant__ DiagAr
   }
 }
 
-// The rate kernels' elementary functions, elementwise (diagnostic): op 0 exp, 1 log, 2 1/x.
+// The rate kernels' elementary functions, elementwise (diagnostic): op 0 exp, 1 log,
+// 2 1/x; 3 and 4 the hi and lo parts of the float-float split (widened exactly).
 __global__ void k_math(int op, const double* x, double* y, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = op == 0 ? xexp(x[i]) : op == 1 ? xlog(x[i]) : xrcp(x[i]);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (op >= 3) {
+      const ff2 s = ff_split(x[i]);
+      y[i] = f32_to_f64(op == 3 ? s.hi : s.lo);
+    } else {
+      y[i] = op == 0 ? xexp(x[i]) : op == 1 ? xlog(x[i]) : xrcp(x[i]);
+    }
+  }
 }
 
 struct LuArgs {
@@ -92,9 +99,9 @@ __global__ void __launch_bounds__(NW * 32) k_lu_solve(const __grid_constant__ Lu
     const double* As = a.A + (size_t)s * n * n;
     for (int i = c.warp; i < n; i += NW)
       for (int j = c.lane; j < n; j += 32) {
-        const typename P::ASM v = (typename P::ASM)As[i * n + j];
+        const double v = As[i * n + j];
         M[i * ld + j] = (R)v;
-        if constexpr (P::IR) reinterpret_cast<typename P::ASM*>(c.M0)[i * ld + j] = v;
+        if constexpr (P::IR) reinterpret_cast<typename P::ASM*>(c.M0)[i * ld + j] = from_double<typename P::ASM>(v);
       }
     for (int i = c.tid; i < n; i += NT) c.fv[i] = a.b[(size_t)s * n + i];
     __syncthreads();

@@ -344,7 +344,7 @@ def test_h0_range_falls_back_to_heuristic(pkg):
     print("cells beyond %d sd: %d of %d (%d near the threshold)" % (z, far.sum(), n, (~clear).sum()))
     assert 0 < far.sum() < n
     runs = {}
-    for name, opts in (("heur", {}), ("learned", {"h0": 1}), ("ranged", {"h0": 1, "h0_range": z})):
+    for name, opts in (("heur", {}), ("learned", {"h0": 1, "h0_range": 0}), ("ranged", {"h0": 1, "h0_range": z})):
         integ = pkg.Integrator(m, precision=1, scheduler=2, **opts)
         if opts:
             model.attach(integ)

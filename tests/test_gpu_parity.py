@@ -103,6 +103,32 @@ def test_jacobian_parity(pkg, orc, name):
             assert err.max() <= tol, (name, precision, c, err.max())
 
 
+@pytest.mark.parametrize("name", list(_mech_cases().keys()))
+def test_float_float_assembly_accuracy(pkg, orc, name):
+    """The mixed form assembles the Jacobian in float-float arithmetic on the FP32 pipe
+    (about 48 significant bits: one FP32 rounding would leave ~6e-8). Entry by entry,
+    relative to |J| plus the row's largest entry, it must agree with the oracle to
+    1e-11 and with the FP64 form's assembly to 1e-11: the accuracy RODAS4 needs of its
+    Jacobian to keep its order, which a plain FP32 assembly (precision 2) does not have."""
+    m = _mech_cases()[name]
+    st = _states(m, n=12)
+    M = orc.Mech(m)
+    J = {}
+    for precision in (0, 1):
+        integ = pkg.Integrator(m, precision=precision)
+        J[precision] = integ.eval_jacobian(_dev(st.T), _dev(st.p), _dev(st.Y)).cpu().numpy()
+    worst = {"oracle": 0.0, "fp64": 0.0}
+    for c in range(st.T.shape[0]):
+        y = np.concatenate([[st.T[c]], st.Y[c]])
+        Jr = orc.jac(M, st.p[c], y)
+        row = np.abs(Jr).max(axis=1, keepdims=True) + 1e-300
+        worst["oracle"] = max(worst["oracle"], (np.abs(J[1][c] - Jr) / (np.abs(Jr) + row)).max())
+        worst["fp64"] = max(worst["fp64"], (np.abs(J[1][c] - J[0][c]) / (np.abs(Jr) + row)).max())
+    print(name, "float-float assembly: max scaled error vs oracle %.2e, vs FP64 form %.2e" %
+          (worst["oracle"], worst["fp64"]))
+    assert worst["oracle"] <= 1e-11 and worst["fp64"] <= 1e-11, worst
+
+
 def _large_gibbs_mechanism():
     """The 54-species mechanism with every formation enthalpy (NASA a6) scaled so the
     largest |a6| is 1.8e5 K: at 300 K the species' |G/RT| reach about 600. Scaling all
@@ -121,7 +147,11 @@ def test_rhs_jacobian_large_gibbs_parity(pkg, orc):
     at 300 K: the kernels' reverse-rate ratio (normally a product of per-species
     factors exp(+-G/RT), whose partial products would leave the double range here)
     must match the oracle's one exponential of the reaction's Gibbs energy change, for
-    the RHS (1e-11) and the Jacobian (1e-10), FP64 and mixed forms."""
+    the RHS (1e-11) and the Jacobian (1e-10), FP64 and mixed forms. The mixed form
+    assembles in float-float, whose exponent range is FP32's: entries below 2^-126
+    (here whole rows of near-inert species at 300 K, next to entries of 1e14) become
+    zero, so its Jacobian error is taken net of that floor (64 x 2^-126, against
+    diagonal entries of the iteration matrix of at least 1/dt)."""
     m = _large_gibbs_mechanism()
     st = _states(m, n=16)
     st.T[:] = np.geomspace(300.0, 2500.0, 16)
@@ -144,7 +174,8 @@ def test_rhs_jacobian_large_gibbs_parity(pkg, orc):
             assert np.all(np.abs(f[c] - fr) <= 1e-11 * (np.abs(fr) + gross) + 1e-300), (precision, c)
             Jr = orc.jac(M, st.p[c], y)
             row = np.abs(Jr).max(axis=1, keepdims=True) + 1e-300
-            err = np.abs(J[c] - Jr) / (np.abs(Jr) + row)
+            floor = 64 * 2.0 ** -126 if precision == 1 else 0.0
+            err = np.maximum(np.abs(J[c] - Jr) - floor, 0.0) / (np.abs(Jr) + row)
             assert err.max() <= 1e-10, (precision, c, err.max())
 
 
@@ -252,6 +283,46 @@ def test_rcp_accuracy(pkg):
     yo = pkg.eval_math("rcp", _dev(xo)).cpu().numpy()
     assert yo[0] == np.inf and yo[1] == -np.inf and yo[2] == 0.0 and np.isnan(yo[3])
     np.testing.assert_allclose(yo[4:], 1 / xo[4:], rtol=2.3e-16)
+
+
+def test_float_float_split(pkg):
+    """The integer-operation split of a double into a float-float pair (the mixed
+    form's assembly and refinement inputs), against its definition computed here
+    from the bit pattern: hi = x with the low 29 mantissa bits cleared, lo = x - hi
+    rounded to FP32 (exactly, where lo is an FP32 normal number; within one subnormal
+    unit where it is not, the integer-to-float rounding coming before the scaling);
+    in FP32's subnormal range hi = x truncated to a multiple of 2^-149 and lo = 0;
+    |x| >= 2^128 gives (+-inf, 0), NaN gives NaN. The widening back to double that
+    returns the parts is exact, subnormals included."""
+    rng = np.random.default_rng(12)
+    x = np.concatenate([10.0 ** rng.uniform(-45, 45, 200000) * rng.choice([-1.0, 1.0], 200000),
+                        rng.uniform(-2.0, 2.0, 50000),
+                        [2.0 ** -126, np.nextafter(2.0 ** -126, 0.0), 2.0 ** 128, np.nextafter(2.0 ** 128, 0.0),
+                         -np.nextafter(2.0 ** 128, 0.0), 1.0, 1.5, -3.0, 2.0 - 2.0 ** -52, 0.0, -0.0,
+                         np.inf, -np.inf, np.nan, 2.0 ** -100, 3.0 * 2.0 ** -100, 2.0 ** -149,
+                         1.5 * 2.0 ** -140, -2.0 ** -127, 2.0 ** -150]])
+    d = _dev(x)
+    hi = pkg.eval_math("ff_hi", d).cpu().numpy()
+    lo = pkg.eval_math("ff_lo", d).cpu().numpy()
+    ax = np.abs(x)
+    normal = (ax >= 2.0 ** -126) & (ax < 2.0 ** 128)
+    u = x[normal].view(np.uint64)
+    hi_ref = (u & ~np.uint64(0x1FFFFFFF)).view(np.float64)
+    np.testing.assert_array_equal(hi[normal], hi_ref)
+    rem = x[normal] - hi_ref  # exact in double
+    lo_ref = rem.astype(np.float32).astype(np.float64)
+    sub = np.abs(lo_ref) < 2.0 ** -126
+    np.testing.assert_array_equal(lo[normal][~sub], lo_ref[~sub])
+    assert np.all(np.abs(lo[normal][sub] - lo_ref[sub]) <= 2.0 ** -149)
+    wide = normal & (ax >= 2.0 ** -100)
+    assert np.all(np.abs(x[wide] - (hi[wide] + lo[wide])) <= 2.0 ** -48 * ax[wide])
+    tiny = ax < 2.0 ** -126
+    q = np.floor(ax[tiny] / 2.0 ** -149) * 2.0 ** -149 * np.sign(x[tiny])
+    np.testing.assert_array_equal(hi[tiny], q)
+    assert np.all(lo[tiny] == 0.0)
+    big = (ax >= 2.0 ** 128) & ~np.isnan(x)
+    assert np.all(hi[big] == np.sign(x[big]) * np.inf) and np.all(lo[big] == 0.0)
+    assert np.isnan(hi[np.isnan(x)]).all()
 
 
 # ------------------------------------------------------------------ LU
