@@ -133,6 +133,29 @@ __device__ __forceinline__ ff2 ff_fma(ff2 a, ff2 b, ff2 c) {
   const ff2 s = two_sum(p.hi, c.hi);
   return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(p.lo, c.lo)));
 }
+// Running float-float sum s + c in the manner of Ogita, Rump and Oishi's Sum2/Dot2:
+// each term's hi part enters s through TwoSum, its rounding error, its lo part and the
+// cross terms of a product gather in c; renormalised once at the end. Each term waits
+// on one FP32 add of the previous one (s and c are separate chains), where a chain of
+// renormalised float-float sums waits on about eight.
+struct ff_sum {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ ff_sum() = default;
+  __device__ __forceinline__ explicit ff_sum(ff2 v) : s(v.hi), c(v.lo) {}
+  __device__ __forceinline__ void add(ff2 v) {
+    const ff2 t = two_sum(s, v.hi);
+    s = t.hi;
+    c = __fadd_rn(c, __fadd_rn(t.lo, v.lo));
+  }
+  __device__ __forceinline__ void add_prod(ff2 a, ff2 b) {
+    const ff2 p = ff_prod(a, b);
+    const ff2 t = two_sum(s, p.hi);
+    s = t.hi;
+    c = __fadd_rn(c, __fadd_rn(t.lo, p.lo));
+  }
+  __device__ __forceinline__ ff2 value() const { return fast_two_sum(s, c); }
+};
+
 // conversions between the matrix element types (double, float, float-float)
 __device__ __forceinline__ float to_float(float a) { return a; }
 __device__ __forceinline__ float to_float(double a) { return (float)a; }
@@ -1326,11 +1349,12 @@ __device__ void assemble_rows_ff(const DevMech& m, Cta<NW>& c, ff2* A, int K, in
   for (int k = c.warp; k < K; k += NW) {
     ff2* row = A + (1 + k) * ld + 1;
     const ff2 beta = beta_ff[k];
-    ff2 acc[U];
+    ff_sum acc[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const unsigned msk = m.jmask[k * U + u];
-      acc[u] = ((msk >> c.lane) & 1u) ? ff_add(beta, row[c.lane + 32 * u]) : beta;
+      acc[u] = ff_sum(beta);
+      if ((msk >> c.lane) & 1u) acc[u].add(row[c.lane + 32 * u]);
     }
     const int t1 = m.tr_ptr[k + 1];
     for (int tb = m.tr_ptr[k]; tb < t1; tb += 32) {
@@ -1350,14 +1374,14 @@ __device__ void assemble_rows_ff(const DevMech& m, Cta<NW>& c, ff2* A, int K, in
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int j = c.lane + 32 * u;
-          if (u < U - 1 || j < K) acc[u] = ff_fma(coef, e[j], acc[u]);
+          if (u < U - 1 || j < K) acc[u].add_prod(coef, e[j]);
         }
       }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int j = c.lane + 32 * u;
-      if (u < U - 1 || j < K) row[j] = ff_fma(acc[u], m.invW_ff[j], j == k ? rf : zero);
+      if (u < U - 1 || j < K) row[j] = ff_fma(acc[u].value(), m.invW_ff[j], j == k ? rf : zero);
     }
   }
 }
@@ -1385,16 +1409,16 @@ __device__ void assemble_ff(const DevMech& m, Cta<NW>& c, const Scal& s, const d
     const int2* se = m.js_ent[v] + c.tid;
     const ff2* sn = m.js_nu_ff[v] + c.tid;
     const int rounds = m.js_rounds[v];
-    ff2 a = zero;
+    ff_sum a;
     for (int r = 0; r < rounds; ++r) {
       const int2 e = se[r * NT];
       if (e.x >= 0) {
         const ff2 w = sn[r * NT];
-        a = ff_fma(JO ? w : ff_neg(w), dq[e.x], a);
+        a.add_prod(JO ? w : ff_neg(w), dq[e.x]);
       }
       if (e.y >= 0) {
-        A[e.y] = a;
-        a = zero;
+        A[e.y] = a.value();
+        a = ff_sum();
       }
     }
   }
@@ -1414,8 +1438,9 @@ __device__ void assemble_ff(const DevMech& m, Cta<NW>& c, const Scal& s, const d
   // (3) temperature row, as in assemble()
   const double ft = s.fT * s.icpm;
   for (int j = NT - 1 - c.tid; j < n; j += NT) {
-    ff2 acc = zero;
-    for (int k = 0; k < K; ++k) acc = ff_fma(ek[k], A[(1 + k) * ld + j], acc);
+    ff_sum sum;
+    for (int k = 0; k < K; ++k) sum.add_prod(ek[k], A[(1 + k) * ld + j]);
+    const ff2 acc = sum.value();
     ff2 v;
     if (j == 0)
       v = ff_sub(ff_sub(rf, acc), ff_split(SG * (s.Scpw * s.irho * s.icpm + ft * s.dcpm)));
