@@ -485,6 +485,13 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
     return o;
   };
   const std::vector<float> eff_ff = split(eff), invW_ff = split(invW), tr_nu_ff = split(tr_nu);
+  // the efficiencies species-major as well: the rate evaluation's [M] sums read one
+  // species for 32 consecutive reactions at a time (coalesced), the assembly one
+  // reaction for 32 consecutive species
+  std::vector<double> effT(eff.size());
+  for (int r = 0; r < n_tb; ++r)
+    for (int k = 0; k < K; ++k) effT[(size_t)k * n_tb + r] = eff[(size_t)r * K + k];
+  const std::vector<float> effT_ff = split(effT);
   std::vector<float> js_nu_ff[3];
   for (int v = 0; v < 3; ++v) js_nu_ff[v] = split(js_nu[v]);
   Pool P;
@@ -497,6 +504,7 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
                oSn = P.add(sp_nu.data(), sp_nu.size() * 8), oTn = P.add(tr_nu.data(), tr_nu.size() * 8),
                oJm = P.add(jmask.data(), jmask.size() * 4),
                oEf = P.add(eff_ff.data(), eff_ff.size() * 4), oiWf = P.add(invW_ff.data(), invW_ff.size() * 4),
+               oEt = P.add(effT.data(), effT.size() * 8), oEtf = P.add(effT_ff.data(), effT_ff.size() * 4),
                oTnf = P.add(tr_nu_ff.data(), tr_nu_ff.size() * 4);
   size_t oJe[3], oJn[3], oJnf[3], oCs[3];
   for (int v = 0; v < 3; ++v) {
@@ -534,6 +542,8 @@ static chem_status build_tables(chem_handle h, const chem_mechanism_desc* d) {
   m.sp_nu = reinterpret_cast<const double*>(b + oSn);
   m.tr_nu = reinterpret_cast<const double*>(b + oTn);
   m.eff_ff = reinterpret_cast<const chem::ff2*>(b + oEf);
+  m.effT = reinterpret_cast<const double*>(b + oEt);
+  m.effT_ff = reinterpret_cast<const chem::ff2*>(b + oEtf);
   m.invW_ff = reinterpret_cast<const chem::ff2*>(b + oiWf);
   m.tr_nu_ff = reinterpret_cast<const chem::ff2*>(b + oTnf);
   m.jmask = reinterpret_cast<const unsigned*>(b + oJm);

@@ -1016,15 +1016,17 @@ __device__ Scal eval_rhs_t(const DevMech& m, Cta<NW>& c, const double* y, double
     double Mc = 0.0, phi = 1.0;
     double dk_dM = 0.0, dlnk = (ar.y + ar.z * invT) * invT, dk_dT = 0.0;
     if (i >= m.i_tb0) {
-      const double* e = m.eff + (size_t)(i - m.i_tb0) * K;
+      // efficiencies species-major: the warp's 32 reactions read one row per species
+      const int r = i - m.i_tb0, ntb = m.n_tb;
       if (FF) {
-        const ff2* ef = m.eff_ff + (size_t)(i - m.i_tb0) * K;
+        const ff2* ef = m.effT_ff + r;
         const ff2* Cf = reinterpret_cast<const ff2*>(c.dk);
         ff2 acc = {0.0f, 0.0f};
-        for (int k = 0; k < K; ++k) acc = ff_fma(ef[k], Cf[k], acc);
+        for (int k = 0; k < K; ++k) acc = ff_fma(ef[(size_t)k * ntb], Cf[k], acc);
         Mc = ff_value(acc);
       } else {
-        for (int k = 0; k < K; ++k) Mc += e[k] * c.C[k];
+        const double* e = m.effT + r;
+        for (int k = 0; k < K; ++k) Mc += e[(size_t)k * ntb] * c.C[k];
       }
       if (i < m.i_fo0) phi = Mc;
     }

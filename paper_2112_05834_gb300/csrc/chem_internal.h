@@ -71,6 +71,8 @@ struct DevMech {
   const double* fo;     // [n_fo][8]: ln(A0/A), b0 - b, Ea0_R - Ea_R, alpha, 1/T***, 1/T*, T**, 0
   const double* eff;    // [n_tb][K] (row r belongs to reaction i_tb0 + r)
   const struct ff2* eff_ff;  // the same efficiencies as float-float pairs (hi, lo)
+  const double* effT;        // [K][n_tb]: the efficiencies species-major
+  const struct ff2* effT_ff;  // the same as float-float pairs
   const int* sp_ptr;    // [K+1] species -> (reaction, nu) CSR
   const int2* sp_ent;
   const double* sp_nu;  // the same nu as doubles
