@@ -197,9 +197,13 @@ chem_status chem_integrate_jobs(const chem_job* jobs, int32_t n_jobs, double dt,
 /*
  * Handle options (numeric values):
  *   "precision"   0 = FP64 throughout;
- *                 1 = mixed: LU and triangular solves in FP32, every solve
- *                 refined by FP64 iterative refinement against the FP64-assembled
- *                 iteration matrix (state, rates, exp/log, error control in FP64);
+ *                 1 = mixed: the iteration matrix assembled in float-float
+ *                 arithmetic (about 48 significant bits, on the FP32 pipe),
+ *                 factorised (Gauss-Jordan inverse) in FP32, every solve refined
+ *                 with residuals against the assembled matrix computed as
+ *                 compensated FP32 dot products (state, rates, exp/log, error
+ *                 control in FP64); matrix entries below 2^-126 in magnitude
+ *                 lose precision (FP32's exponent range);
  *                 2 = as 1 but with the Jacobian assembled in FP32 and the
  *                 refinement residual taken against that FP32 matrix
  *   "ir_sweeps"   0..3 refinement sweeps per solve in precision 1 and 2 (default 1)
@@ -383,8 +387,9 @@ chem_status chem_eval_h0(chem_handle h, int64_t n_cells, const double* T, const 
 /*
  * Batched dense solve with the integrator's LU and triangular-solve code:
  * for each of n_mat systems, A[dim][dim] x = b (device, row-major, A unchanged).
- * precision 0: FP64 LU; 1: FP32 LU of A with `ir_sweeps` FP64 refinement sweeps
- * against A; 2: as 1 against A rounded to FP32.
+ * precision 0: FP64 LU; 1: FP32 Gauss-Jordan inverse of A with `ir_sweeps`
+ * refinement sweeps against A held as float-float pairs (residuals as compensated
+ * FP32 dot products, about 48 bits); 2: as 1 against A rounded to FP32.
  * info[n_mat] (device, may be NULL): 0, or 1+k for a zero pivot at column k.
  * dim <= 128.
  */
