@@ -7,7 +7,8 @@ each time. Default workload: the 54-species / 270-reaction synthetic mechanism,
 
 Forms timed on the GPU:
   plain_fp64 : FP64 throughout, one CTA per cell (the plain batched baseline)
-  headline   : mixed precision (FP32 LU/solves + FP64 refinement), persistent
+  headline   : mixed precision (float-float Jacobian assembly, FP32 Gauss-Jordan and
+               solves, refinement against the float-float matrix), persistent
                work queue, and (when trained) the learned cost order and initial
                step.
 The JSON line's value is the headline form; plain_fp64 is reported beside it.
@@ -938,7 +939,7 @@ def main():
             "substeps_per_step": wm["substeps"], "rejects_per_step": wm["rejects"], "failed_cells": wm["failed"],
             "headline_substeps_per_step": hd["substeps"], "headline_rejects_per_step": hd["rejects"],
             "speed_vs_headline": wv / value,
-            "form": "ROS34PW2 W-method, Jacobian assembled in FP32, FP32 Gauss-Jordan, FP64 refinement "
+            "form": "ROS34PW2 W-method, Jacobian assembled in FP32, FP32 Gauss-Jordan, refinement "
                     "against the FP32 matrix, queue"}
         if "phases" in wm:
             line["w_method_fp32_assembly"]["phase_share"] = wm["phases"]

@@ -820,7 +820,7 @@ chem_status chem_internal_integrate(const chem_job* jobs, int32_t n_jobs, double
     h0->err = "chem_integrate: mechanism too large for shared memory";
     return CHEM_ERR_INVALID_ARG;
   }
-  // the mixed form may keep its FP64 matrix in global memory on persistent grids when
+  // the mixed form may keep its assembled matrix in global memory on persistent grids when
   // that lets more CTAs share an SM (large mechanisms)
   const bool m0g_ok = h0->precision == PREC_MIXED && a.sched != SCHED_PLAIN;
   int block = h0->block ? h0->block : chem_internal_pick_block(h0, a.smem_K, a.smem_I, m0g_ok);

@@ -37,7 +37,7 @@ struct chem_handle_s {
   int autotune = 0;
   int profile = 0;
   unsigned long long* d_phase = nullptr;  // [8] per-phase cycle counters (option "profile")
-  double* d_m0 = nullptr;                 // per-CTA slots of the mixed form's FP64 matrix (large mechanisms)
+  double* d_m0 = nullptr;                 // per-CTA slots of the mixed form's assembled matrix
   size_t m0_cap = 0;                      // bytes
   int time_kernel = 0;                    // option "time_kernel": events around the integration launch
   int jac_fd = 0;                         // option "jacobian": 1 = forward differences (FP64 form)
@@ -98,7 +98,7 @@ struct chem_handle_s {
   long long autotuned_key = -1;
   int autotuned_block = 128;
   int autotuned_ctas = 0;   // 0: as many as fit
-  int autotuned_m0g = -1;   // mixed form's FP64 matrix: 0 shared memory, 1 global slot, -1 automatic
+  int autotuned_m0g = -1;   // mixed form's assembled matrix: 0 shared memory, 1 global slot, -1 automatic
   std::string err;
 };
 

@@ -9,8 +9,8 @@
 // form inverts in FP32 with the matrix in registers (columns over warps, rows over
 // lanes) and solves by matrix-vector products over all threads. All per-cell data
 // (state, stage vectors, per-reaction derivative data, the iteration matrix) lives
-// in shared memory, except that the mixed form may keep its FP64 assembled matrix
-// in a global-memory slot of the CTA when that lets more CTAs share an SM; the
+// in shared memory, except that the mixed form may keep its assembled matrix (float-
+// float pairs) in a global-memory slot of the CTA when that lets more CTAs share an SM; the
 // mechanism tables are read through the L1 cache.
 //
 // Paper mapping: rates and RHS = pyJac's reaction-rate evaluation; analytic
@@ -709,7 +709,7 @@ __host__ __device__ inline int odd_ld(int n) { return n | 1; }
 // vectors (double): y, yn, ys, f0, fv, rr, u[6], sc  -> 13 n
 // species (double): C, hRT, cpR, eg, dcp, dk, akT, ek, ieg -> 9 K
 // reactions (double): q, D, dTc, P, dqs[4] -> 8 I
-// m0_global: the mixed form's FP64 assembled matrix lives in a global-memory slot of
+// m0_global: the mixed form's assembled matrix lives in a global-memory slot of
 // the CTA instead of shared memory (large mechanisms, persistent schedulers).
 __host__ __device__ inline Layout make_layout(int Kmax, int Imax, int prec, bool m0_global = false) {
   Layout L;

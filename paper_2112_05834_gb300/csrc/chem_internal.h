@@ -18,8 +18,9 @@ constexpr double kTmin = 200.0, kTmax = 6000.0;
 constexpr double kBigGRT = 150.0;
 
 // FP64: everything in FP64.
-// MIXED: Jacobian assembled in FP64 (kept for the refinement residual), LU and
-//        triangular solves in FP32, FP64 iterative refinement of every solve.
+// MIXED: Jacobian assembled in float-float arithmetic (about 48 bits, FP32 pipe; kept
+//        for the refinement residual), FP32 Gauss-Jordan inverse and solves, every
+//        solve refined with residuals computed as compensated FP32 dot products.
 // FP32ASM: Jacobian assembled in FP32 as well; refinement residual against the
 //        FP32-assembled matrix (kept for comparison: it perturbs the method).
 enum Precision { PREC_FP64 = 0, PREC_MIXED = 1, PREC_FP32ASM = 2 };
@@ -129,8 +130,8 @@ struct IntegrateArgs {
   int no_pivot;        // FP64 form only: 1 = Gaussian elimination without row interchanges
   int smem_K, smem_I;  // sizes the shared-memory carve-up was computed for
   unsigned long long* phase;  // optional [8] per-phase cycle counters (diagnostic)
-  double* m0_scratch;  // mixed form, persistent grids: per-CTA slots for the FP64 assembled
-  int64_t m0_stride;   //   matrix (null: it stays in shared memory); doubles per slot
+  double* m0_scratch;  // mixed form, persistent grids: per-CTA slots for the assembled matrix
+  int64_t m0_stride;   //   (8-byte entries; null: it stays in shared memory); entries per slot
   MethodTab tab;       // the Rosenbrock method
 };
 

@@ -248,7 +248,7 @@ static void cache_store(long long key, int block, int ctas, int m0g) {
 }
 
 // Candidates: CTA size (2, 4 or 8 warps on one cell) x matrix layout of the mixed form
-// (FP64 assembled matrix in shared memory, or in a per-CTA global slot, which leaves room
+// (assembled matrix in shared memory, or in a per-CTA global slot, which leaves room
 // for more CTAs) x resident CTAs per SM on persistent grids (as many as fit, or one
 // fewer: fewer CTAs compete for the SM's FP64 pipe and issue slots). Each is timed on a
 // sample of the call's cells (copies; the caller's arrays are not touched), one warm-up
