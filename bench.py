@@ -144,6 +144,16 @@ def algorithmic_fp64_flops_per_step(m, precision, ir_sweeps):
     return float(w)
 
 
+def float_float_flops_per_step(m, ir_sweeps):
+    """The part of algorithmic_fp64_flops_per_step (mixed form) that the kernel runs as
+    float-float arithmetic on the FP32 pipe: the third-body sums of the 7 RHS evaluations,
+    the Jacobian assembly and the refinement residuals."""
+    K = m.n_species
+    n = K + 1
+    n_tb = int(np.sum(m.rxn_type >= 1))
+    return float(7 * 2 * n_tb * K + 6 * n * n + 6 * ir_sweeps * 2 * n * n)
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
 
@@ -888,6 +898,7 @@ def main():
     # launch (per-step work x the Rosenbrock steps the launch took) / its event-timed
     # duration averaged over the timed steps
     w_step = algorithmic_fp64_flops_per_step(m, 1, 1)
+    ff_share = float_float_flops_per_step(m, 1) / w_step
     substeps_per_launch = hd["substeps"]  # totals of the last launch
     achieved = w_step * substeps_per_launch / (hd["kernel_ms"] / 1e3) / 1e12
     line = {
@@ -904,8 +915,12 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS, "traffic": kernel_traffic(n),
                      "kernel": "chem::k_integrate<4, mixed>", "kernel_ms": hd["kernel_ms"],
-                     "note": "FP64 pipe; algorithmic FP64 flops per launch / CUDA-event launch time; peak "
-                             "derived: 2 DFMA/clk/SM x 152 SMs x 2 flop x 2070 MHz"},
+                     "float_float_share": ff_share,
+                     "fp64_executed_frac": achieved * (1.0 - ff_share) / FP64_PEAK_TFLOPS,
+                     "note": "FP64 pipe; algorithmic FP64-precision flops per launch / CUDA-event launch time; "
+                             "float_float_share of them (third-body sums, Jacobian assembly, refinement "
+                             "residuals) run as float-float arithmetic on the FP32 pipe, fp64_executed_frac "
+                             "counts the rest only; peak derived: 2 DFMA/clk/SM x 152 SMs x 2 flop x 2070 MHz"},
         "clocks": clk,
         "e2e": {"value": world * n * args.steps / e2e_s, "unit": "cells*step/s",
                 "h2d_bytes_per_step": int(n * (m.n_species + 2) * 8), "d2h_bytes_per_step": int(n * (m.n_species + 1) * 8)},
