@@ -203,7 +203,10 @@ chem_status chem_integrate_jobs(const chem_job* jobs, int32_t n_jobs, double dt,
  *                 with residuals against the assembled matrix computed as
  *                 compensated FP32 dot products (state, rates, exp/log, error
  *                 control in FP64); matrix entries below 2^-126 in magnitude
- *                 lose precision (FP32's exponent range);
+ *                 lose precision and entries of 2^128 or more overflow (FP32's
+ *                 exponent range: a cell whose iteration matrix overflows fails
+ *                 its steps and ends with a failure status; precision 0 has the
+ *                 FP64 range);
  *                 2 = as 1 but with the Jacobian assembled in FP32 and the
  *                 refinement residual taken against that FP32 matrix
  *   "ir_sweeps"   0..3 refinement sweeps per solve in precision 1 and 2 (default 1)
