@@ -38,7 +38,7 @@ namespace chem {
 #define FULLMASK 0xffffffffu
 
 // ---------------------------------------------------------------------------
-// Float-float arithmetic (a value is hi + lo with two FP32 numbers, |lo| <= ulp(hi)/2):
+// Float-float arithmetic (a value is hi + lo with two FP32 numbers, |lo| below ulp(hi)):
 // error-free products with FMA (Dekker's TwoProduct) and sums by Knuth's TwoSum
 // give about 44-48 significant bits on the FP32 pipe. On GB300 an SM's FP32 pipe
 // completes 64 times the operations per clock of its FP64 pipe, which the
@@ -910,6 +910,8 @@ struct Scal {
 // ratio then takes one exponential of the summed exponent per reaction instead of
 // the product of four species factors, whose partial products could overflow or
 // underflow. A separate instantiation, so that the common path carries no trace of it.
+// FF (the forms with FP32 factors): the third-body sums [M] in float-float, and the
+// slot derivatives and P stored as float-float pairs for the assembly.
 template <int NW, bool JAC, bool FF, bool BIG>
 __device__ Scal eval_rhs_t(const DevMech& m, Cta<NW>& c, const double* y, double p, double* f) {
   constexpr int NT = NW * 32;
