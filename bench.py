@@ -77,6 +77,9 @@ def parse():
     ap.add_argument("--retrain-every", type=int, default=0,
                     help="with --cfd-loop: retrain the model every N steps on the learned form's own logs "
                          "of the last N steps (0: train once, on steps 1-5)")
+    ap.add_argument("--retrain-epochs", type=int, default=20,
+                    help="with --retrain-every: epochs of each retraining (continuing from the current "
+                         "weights)")
     ap.add_argument("--no-h0-guard", action="store_true",
                     help="with --cfd-loop: the learned initial step as predicted, without the starting-step "
                          "envelope check (option h0_guard = 0)")
@@ -765,10 +768,11 @@ def run_cfd_loop(args):
         if args.retrain_every and step > 6 and (step - 6) % args.retrain_every == 0 and logs:
             t0 = time.perf_counter()
             cat = [torch.cat([lg[k] for lg in logs]) for k in range(5)]
-            losses = model.train(*cat, epochs=20, batch=8192, lr=1e-3, seed=12 + step)
+            losses = model.train(*cat, epochs=args.retrain_epochs, batch=8192, lr=1e-3, seed=12 + step)
             torch.cuda.synchronize()
             line["train_s"] = time.perf_counter() - t0
             line["train_loss"] = [float(losses[0]), float(losses[-1])]
+            tot["retrain_s"] = tot.get("retrain_s", 0.0) + line["train_s"]
             model.attach(learned)
             logs.clear()
         T, Y, ms, s = timed(plain, T0, p, Y0)
@@ -811,11 +815,14 @@ def run_cfd_loop(args):
         st = synth.perturb_states(synth.CellStates(T=T.cpu().numpy(), p=st.p, Y=Y.cpu().numpy(), kind=st.kind),
                                   seed=100 + step)
     print(json.dumps({"cfd_loop_summary": "steps 6-20", "n_cells": n, "retrain_every": args.retrain_every,
+                      "retrain_epochs": args.retrain_epochs if args.retrain_every else None,
+                      "retrain_s_total": tot.get("retrain_s", 0.0),
                       "learned_order": not args.no_learned_order, "h0_guard": not args.no_h0_guard,
                       "h0_range": args.h0_range,
                       "plain_cells_step_per_s": 15 * n / (tot["plain_ms"] / 1e3),
                       "learned_cells_step_per_s": 15 * n / (tot["learned_ms"] / 1e3),
                       "speedup": tot["plain_ms"] / tot["learned_ms"],
+                      "speedup_incl_retraining": tot["plain_ms"] / (tot["learned_ms"] + 1e3 * tot.get("retrain_s", 0.0)),
                       "substeps_ratio": tot["learned_sub"] / tot["plain_sub"]}), flush=True)
 
 
