@@ -87,3 +87,24 @@ def test_reference_arm_two_gloo_ranks(built_oracle):
     assert len(lines) == 1  # rank 0 only
     _check_line(lines[0])
     assert lines[0]["n_gpus"] == 2
+
+
+def test_flop_model_split():
+    """The roofline's flop model: the float-float part (third-body sums of the 7 RHS
+    evaluations, assembly 6 n^2, residuals 12 n^2 per sweep) is a part of the mixed
+    form's count, counted term by term here for the 54-species workload."""
+    import bench
+    from paper_2112_05834_gb300 import synth
+
+    m, _, _ = synth.workload("c54_65k", n_cells=4)
+    K, I = m.n_species, m.n_reactions
+    n = K + 1
+    n_tb = int((m.rxn_type >= 1).sum())
+    n_fo = int((m.rxn_type >= 2).sum())
+    total = bench.algorithmic_fp64_flops_per_step(m, 1, 1)
+    assert total == 7 * (41 * K + 22 * I + 2 * n_tb * K + 30 * n_fo) + 24 * I + 6 * n * n + 12 * n * n
+    ff = bench.float_float_flops_per_step(m, 1)
+    assert ff == 7 * 2 * n_tb * K + 6 * n * n + 12 * n * n
+    assert 0.0 < ff < total
+    # more refinement sweeps add residual flops to both counts alike
+    assert bench.float_float_flops_per_step(m, 3) - ff == bench.algorithmic_fp64_flops_per_step(m, 1, 3) - total
